@@ -1,0 +1,197 @@
+/* sfsim.h - C ABI of the GB300 Schroedinger-Feynman simulator of random grid
+ * circuits (arXiv:1807.10749, "Quantum Supremacy Is Both Closer and Farther
+ * than It Appears").
+ *
+ * The problem statement follows Section 2 and Section 3 of the paper: a
+ * circuit on a qubit grid, a straight cut of the grid into two blocks, a set of
+ * simulation paths (all of them, or a fraction f for fidelity ~ f) and a list of
+ * requested bitstrings go in; the amplitudes <x|U|0...0> summed over the
+ * selected paths come out.
+ *
+ * Conventions used by every call:
+ *   - Qubit q of an R x C grid sits at row q / C, column q % C (row-major).
+ *   - Bit q of a bitstring (uint64) is the measured value of qubit q.
+ *   - Complex numbers are interleaved (re, im) doubles.
+ *   - Every function returns an int status: SF_OK (0) or a negative SF_E*
+ *     code. sf_last_error() returns the message of the calling thread's last
+ *     failure. No C++ exception crosses this interface.
+ *   - Inputs are copied during the call; the library never frees or keeps a
+ *     caller pointer after it returns (except the server, which copies the
+ *     submitted arrays). Output buffers are owned by the caller.
+ *   - Device pointers (the *_device calls) are CUDA global-memory pointers of
+ *     the current device; streams are cudaStream_t passed as void*.
+ *   - Not thread-safe per object: a plan or a server handle must not be used
+ *     by two threads at once. Different handles are independent.
+ */
+#ifndef SFSIM_H
+#define SFSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SF_API __attribute__((visibility("default")))
+#else
+#define SF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SF_OK = 0,
+  SF_EINVAL = -1,       /* bad argument: gate, qubit, cut, size, selection */
+  SF_ENOMEM = -2,       /* host or device memory, or a budget too small */
+  SF_ECUDA = -3,        /* a CUDA call failed (message in sf_last_error) */
+  SF_ETIMEOUT = -4,     /* sf_server_wait: not finished within the timeout */
+  SF_ECANCELLED = -5,   /* the request was cancelled */
+  SF_EUNSUPPORTED = -6  /* valid input this build does not handle */
+};
+
+/* Gate kinds. Matrices (Section 1 gate set; Eq. 1 for CZ; Section 7 for iSWAP):
+ *   SF_H = (1/sqrt2)[[1,1],[1,-1]]    SF_T = diag(1, e^{i pi/4})
+ *   SF_X_HALF = 1/2 [[1+i,1-i],[1-i,1+i]]   SF_Y_HALF = 1/2 [[1+i,-1-i],[1+i,1+i]]
+ *   SF_Z = diag(1,-1)   SF_S = diag(1,i)   SF_CZ = diag(1,1,1,-1)
+ *   SF_ISWAP = |00><00| + i|01><10| + i|10><01| + |11><11|
+ *   SF_U1: 2x2 from m[0..8); SF_U2: 4x4 from m[0..32), row-major, on the basis
+ *   index 2*bit(q0) + bit(q1). */
+enum sf_gate_kind { SF_H = 0, SF_X_HALF, SF_Y_HALF, SF_T, SF_Z, SF_S, SF_CZ, SF_ISWAP, SF_U1, SF_U2 };
+
+typedef struct {
+  int32_t cycle;   /* clock cycle; gates of one cycle act on disjoint qubits */
+  int32_t kind;    /* sf_gate_kind */
+  int32_t q0, q1;  /* qubits (q1 ignored for one-qubit kinds) */
+  double m[32];    /* SF_U1 / SF_U2 entries (re, im interleaved) */
+} sf_gate;
+
+typedef struct sf_circuit sf_circuit;
+typedef struct sf_plan sf_plan;
+typedef struct sf_server sf_server;
+
+/* Build a circuit on a rows x cols grid (n = rows*cols <= 64) from n_gates
+ * gates in time order. Copies the gates. Fails with SF_EINVAL on a bad qubit,
+ * kind, a two-qubit gate on one qubit, or two gates of one cycle sharing a
+ * qubit. */
+SF_API int sf_circuit_create(int rows, int cols, const sf_gate* gates, int64_t n_gates, sf_circuit** out);
+
+/* Parse the text format (NUL-terminated): a 'grid R C' line, then
+ * '<cycle> <name> <qubits> [reals]' lines, names h t x_1_2 y_1_2 z s cz iswap
+ * u1 u2; '#' starts a comment. */
+SF_API int sf_circuit_parse(const char* spec_text, sf_circuit** out);
+SF_API int sf_circuit_info(const sf_circuit* c, int* rows, int* cols, int64_t* n_gates);
+SF_API void sf_circuit_destroy(sf_circuit* c);
+
+/* Cross-gate decompositions (Section 2 footnote, Section 3, Section 7). CZ
+ * always uses Eq. 1 (P0 (x) I + P1 (x) Z, projector on the half-A qubit). */
+enum { SF_DEC_SCHMIDT = 0, /* operator-Schmidt (SVD of the realigned matrix) */
+       SF_DEC_BLOCK4 = 1   /* Eq. 4way: P0, P1, |0><1|, |1><0| on the A side */ };
+enum { SF_EXEC_BATCHED = 0, /* path tree, batched launches, deferred last level */
+       SF_EXEC_PLAIN = 1    /* every path from the prefix checkpoint alone */ };
+
+typedef struct {
+  uint64_t side_b_mask;      /* bit q set: qubit q in half B; 0 = automatic
+                                straight cut (Section 8: minimise the larger
+                                block, then the number of cross gates) */
+  int32_t decomposition;     /* SF_DEC_* for non-CZ cross gates */
+  int32_t select_prefix_bits;/* x_s of FRACTION selection; -1 = max(0, x-7) */
+  int32_t tile_bits;         /* log2 amplitudes per tile, 0 = tuned default */
+  int32_t fuse_bits;         /* log2 amplitudes per thread register block
+                                (fusion width), 0 = tuned default */
+  int32_t exec_mode;         /* SF_EXEC_* */
+  int32_t defer_last_level;  /* 1 (default) / 0: fold the last branch level
+                                into the gather when the circuit allows */
+  int64_t hbm_budget_bytes;  /* device memory the executor may use, 0 = 75% of
+                                free memory at plan time */
+  int32_t batch_paths;       /* max leaf groups per launch, 0 = from budget */
+  int32_t reserved[7];
+} sf_plan_opts;
+
+SF_API void sf_plan_opts_default(sf_plan_opts* o);
+
+/* Plan the simulation: cut, cross gates (time order (cycle, lower qubit,
+ * higher qubit)), decomposition, path tree, fused passes. Uses the current
+ * CUDA device (uploads the pass programs). */
+SF_API int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out);
+
+/* n_cross: cross gates; path_bits: log2 of the path count (each cross gate
+ * contributes log2 of its term count, 1 for CZ); m_a / m_b: half sizes;
+ * n_levels: branching levels (cycles with cross gates). Any pointer may be
+ * NULL. */
+SF_API int sf_plan_info(const sf_plan* p, int* n_cross, int* path_bits, int* m_a, int* m_b, int* n_levels);
+
+/* Planner statistics: passes per half over the whole circuit, register
+ * stages, deferred gates at the last level. */
+SF_API int sf_plan_stats(const sf_plan* p, int* passes_a, int* passes_b, int* stages_a, int* stages_b,
+                  int* deferred);
+SF_API void sf_plan_destroy(sf_plan* p);
+
+/* Path selection (Eq. 3; Section 3). Path ids number the branch choices, the
+ * earliest cross gate in the most significant bits.
+ *   SF_SEL_RANGE: ids first .. first+count-1.
+ *   SF_SEL_FRACTION: K = max(1, floor(fidelity * 2^xs + 1e-9)) prefixes of xs
+ *     bits, the images of 0..K-1 under the keyed Feistel permutation (key =
+ *     seed), each with all its suffixes; xs = the plan's select_prefix_bits.
+ *   SF_SEL_LIST: the n_list ids in list (any order, duplicates rejected). */
+enum { SF_SEL_RANGE = 0, SF_SEL_FRACTION = 1, SF_SEL_LIST = 2 };
+typedef struct {
+  int32_t mode;
+  uint64_t first, count;
+  double fidelity;
+  uint64_t seed;
+  const uint64_t* list;
+  int64_t n_list;
+} sf_path_sel;
+
+/* Number of selected paths and f_actual = selected / 2^path_bits. */
+SF_API int sf_selection_size(const sf_plan* p, const sf_path_sel* sel, uint64_t* n_paths, double* f_actual);
+
+/* Write the selected path ids in increasing order into ids[0..cap) (host).
+ * *n_written = min(selected, cap). The enumeration the executor sums. */
+SF_API int sf_selection_ids(const sf_plan* p, const sf_path_sel* sel, uint64_t* ids, uint64_t cap,
+                     uint64_t* n_written);
+
+/* Amplitudes, host buffers: out_amps[2*i], out_amps[2*i+1] = sum over the
+ * selected paths of A_j[x_A] * B_j[x_B] for bitstrings[i] (Eq. 2 / Eq. 3, no
+ * renormalisation by f). out_f_actual may be NULL. Allocates and frees its
+ * device memory inside the call; blocks until done. */
+SF_API int sf_amplitudes(sf_plan* p, const uint64_t* bitstrings, int64_t n, const sf_path_sel* sel,
+                  double* out_amps, double* out_f_actual);
+
+/* Device form: bytes of device workspace sf_amplitudes_device needs. */
+SF_API int sf_workspace_size(const sf_plan* p, int64_t n, const sf_path_sel* sel, size_t* bytes);
+
+/* Device form: d_bitstrings (n uint64) and d_out_amps (2n doubles) are device
+ * pointers; d_workspace of ws_bytes >= sf_workspace_size(). All work is
+ * enqueued on cuda_stream; the call returns after the last launch is enqueued
+ * and the result is valid once the stream reaches it. With accumulate != 0 the
+ * sums are added to d_out_amps; otherwise d_out_amps is overwritten. */
+SF_API int sf_amplitudes_device(sf_plan* p, const uint64_t* d_bitstrings, int64_t n, const sf_path_sel* sel,
+                         double* d_out_amps, int accumulate, void* d_workspace, size_t ws_bytes,
+                         void* cuda_stream);
+
+/* Request server (continuous batching): requests are admitted while their
+ * device footprint fits hbm_budget_bytes; admitted requests run concurrently
+ * on their own streams. Each request's result equals sf_amplitudes on the same
+ * input. */
+SF_API int sf_server_create(int64_t hbm_budget_bytes, int max_concurrent, sf_server** out);
+/* Copies bitstrings and the selection's list. The plan must outlive the
+ * request. */
+SF_API int sf_server_submit(sf_server* s, sf_plan* p, const uint64_t* bitstrings, int64_t n,
+                     const sf_path_sel* sel, uint64_t* ticket);
+/* Waits up to timeout_ms (<0: forever). On SF_OK copies 2n doubles into
+ * out_amps and releases the ticket; SF_ETIMEOUT keeps it. */
+SF_API int sf_server_wait(sf_server* s, uint64_t ticket, int timeout_ms, double* out_amps);
+/* Cancels a queued or running request; its wait returns SF_ECANCELLED. */
+SF_API int sf_server_cancel(sf_server* s, uint64_t ticket);
+/* Seconds from submit to admission and to completion of a finished ticket
+ * (before its wait), for latency reports. */
+SF_API int sf_server_times(sf_server* s, uint64_t ticket, double* queued_s, double* total_s);
+SF_API void sf_server_destroy(sf_server* s);
+
+SF_API const char* sf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFSIM_H */

@@ -1,0 +1,310 @@
+// C ABI of the sfsim library (include/sfsim.h). Every entry point converts
+// internal failures into a status code and a thread-local message.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "sf_internal.h"
+
+struct sf_circuit {
+  sf::Circuit c;
+};
+
+struct HostBuffers {
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  uint64_t* bits = nullptr;
+  double* out = nullptr;
+  int64_t cap_n = 0;
+  cudaStream_t stream = nullptr;
+};
+
+struct sf_plan {
+  sf::Plan* p = nullptr;
+  HostBuffers hb;
+};
+
+namespace sf {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+}  // namespace sf
+
+using sf::Error;
+
+#define SF_GUARD_BEGIN try {
+#define SF_GUARD_END                                  \
+  }                                                   \
+  catch (const Error& e) {                            \
+    sf::set_error(e.msg);                             \
+    return e.code;                                    \
+  }                                                   \
+  catch (const std::bad_alloc&) {                     \
+    sf::set_error("host allocation failed");          \
+    return SF_ENOMEM;                                 \
+  }                                                   \
+  catch (const std::exception& e) {                   \
+    sf::set_error(e.what());                          \
+    return SF_EINVAL;                                 \
+  }                                                   \
+  catch (...) {                                       \
+    sf::set_error("unknown internal error");          \
+    return SF_EINVAL;                                 \
+  }
+
+static void cuda_check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) sf::fail(e == cudaErrorMemoryAllocation ? SF_ENOMEM : SF_ECUDA,
+                                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" {
+
+const char* sf_last_error(void) { return sf::g_last_error.c_str(); }
+
+int sf_circuit_create(int rows, int cols, const sf_gate* gates, int64_t n_gates, sf_circuit** out) {
+  SF_GUARD_BEGIN
+  if (!out) sf::fail(SF_EINVAL, "null output pointer");
+  *out = nullptr;
+  sf::Circuit* c = sf::circuit_from_gates(rows, cols, gates, n_gates);
+  sf_circuit* h = new sf_circuit();
+  h->c = *c;
+  delete c;
+  *out = h;
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_circuit_parse(const char* text, sf_circuit** out) {
+  SF_GUARD_BEGIN
+  if (!out) sf::fail(SF_EINVAL, "null output pointer");
+  *out = nullptr;
+  sf::Circuit* c = sf::circuit_parse(text);
+  sf_circuit* h = new sf_circuit();
+  h->c = *c;
+  delete c;
+  *out = h;
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_circuit_info(const sf_circuit* c, int* rows, int* cols, int64_t* n_gates) {
+  SF_GUARD_BEGIN
+  if (!c) sf::fail(SF_EINVAL, "null circuit");
+  if (rows) *rows = c->c.rows;
+  if (cols) *cols = c->c.cols;
+  if (n_gates) *n_gates = (int64_t)c->c.gates.size();
+  return SF_OK;
+  SF_GUARD_END
+}
+
+void sf_circuit_destroy(sf_circuit* c) { delete c; }
+
+void sf_plan_opts_default(sf_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->decomposition = SF_DEC_SCHMIDT;
+  o->select_prefix_bits = -1;
+  o->exec_mode = SF_EXEC_BATCHED;
+  o->defer_last_level = 1;
+}
+
+int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out) {
+  SF_GUARD_BEGIN
+  if (!c || !out) sf::fail(SF_EINVAL, "null argument");
+  *out = nullptr;
+  sf_plan_opts o;
+  if (opts) o = *opts;
+  else sf_plan_opts_default(&o);
+  if (o.decomposition != SF_DEC_SCHMIDT && o.decomposition != SF_DEC_BLOCK4)
+    sf::fail(SF_EINVAL, "unknown decomposition");
+  if (o.exec_mode != SF_EXEC_BATCHED && o.exec_mode != SF_EXEC_PLAIN) sf::fail(SF_EINVAL, "unknown exec mode");
+  if (o.tile_bits < 0 || o.tile_bits > sf::MAX_K) sf::fail(SF_EINVAL, "tile_bits out of range (0..14)");
+  if (o.fuse_bits < 0 || o.fuse_bits > sf::MAX_R) sf::fail(SF_EINVAL, "fuse_bits out of range (0..5)");
+  if (o.hbm_budget_bytes < 0 || o.batch_paths < 0) sf::fail(SF_EINVAL, "negative budget or batch");
+  if (o.exec_mode == SF_EXEC_PLAIN) {
+    o.defer_last_level = 0;
+    o.batch_paths = 1;
+  }
+  sf::Plan* p = sf::plan_create(c->c, o);
+  sf_plan* h = new sf_plan();
+  h->p = p;
+  *out = h;
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_plan_info(const sf_plan* h, int* n_cross, int* path_bits, int* m_a, int* m_b, int* n_levels) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  const sf::Plan& p = *h->p;
+  if (n_cross) *n_cross = (int)p.cross.size();
+  if (path_bits) *path_bits = p.path_bits;
+  if (m_a) *m_a = p.A.m;
+  if (m_b) *m_b = p.B.m;
+  if (n_levels) *n_levels = (int)p.levels.size();
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_plan_stats(const sf_plan* h, int* passes_a, int* passes_b, int* stages_a, int* stages_b,
+                  int* deferred) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  const sf::Plan& p = *h->p;
+  int pa = 0, pb = 0, sa = 0, sb = 0;
+  for (auto& s : p.A.seg) {
+    pa += (int)s.passes.size();
+    sa += s.n_stages;
+  }
+  for (auto& s : p.B.seg) {
+    pb += (int)s.passes.size();
+    sb += s.n_stages;
+  }
+  if (passes_a) *passes_a = pa;
+  if (passes_b) *passes_b = pb;
+  if (stages_a) *stages_a = sa;
+  if (stages_b) *stages_b = sb;
+  if (deferred) *deferred = p.deferred ? p.levels.back().n_cross : 0;
+  return SF_OK;
+  SF_GUARD_END
+}
+
+// Device-side state of a plan, created on first use (plan creation itself
+// makes no CUDA call): the gather byte tables and the memory budget.
+static void ensure_device(sf::Plan& p) {
+  if (p.d_tabA) return;
+  cuda_check(cudaGetDevice(&p.device), "cudaGetDevice");
+  if (p.opts.hbm_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cuda_check(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+    p.opts.hbm_budget_bytes = (int64_t)(fr / 4 * 3);
+  }
+  uint32_t *a = nullptr, *b = nullptr;
+  try {
+    cuda_check(cudaMalloc(&a, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
+    cuda_check(cudaMalloc(&b, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
+    cuda_check(cudaMemcpy(a, p.A.tab.data(), 8 * 256 * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+    cuda_check(cudaMemcpy(b, p.B.tab.data(), 8 * 256 * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+  } catch (...) {
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    throw;
+  }
+  p.d_tabA = a;
+  p.d_tabB = b;
+}
+
+static void free_host_buffers(HostBuffers& hb) {
+  if (hb.ws) cudaFree(hb.ws);
+  if (hb.bits) cudaFree(hb.bits);
+  if (hb.out) cudaFree(hb.out);
+  if (hb.stream) cudaStreamDestroy(hb.stream);
+  hb = HostBuffers();
+}
+
+void sf_plan_destroy(sf_plan* h) {
+  if (!h) return;
+  free_host_buffers(h->hb);
+  if (h->p) {
+    if (h->p->d_tabA) cudaFree(h->p->d_tabA);
+    if (h->p->d_tabB) cudaFree(h->p->d_tabB);
+    sf::plan_destroy(h->p);
+  }
+  delete h;
+}
+
+int sf_selection_size(const sf_plan* h, const sf_path_sel* sel, uint64_t* n_paths, double* f_actual) {
+  SF_GUARD_BEGIN
+  if (!h || !sel) sf::fail(SF_EINVAL, "null argument");
+  double fa = 0;
+  auto rs = sf::select_ranges(*h->p, *sel, &fa);
+  uint64_t n = 0;
+  for (auto& r : rs) n += r.hi - r.lo;
+  if (n_paths) *n_paths = n;
+  if (f_actual) *f_actual = fa;
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_selection_ids(const sf_plan* h, const sf_path_sel* sel, uint64_t* ids, uint64_t cap,
+                     uint64_t* n_written) {
+  SF_GUARD_BEGIN
+  if (!h || !sel || (cap && !ids)) sf::fail(SF_EINVAL, "null argument");
+  double fa = 0;
+  auto rs = sf::select_ranges(*h->p, *sel, &fa);
+  uint64_t w = 0;
+  for (auto& r : rs)
+    for (uint64_t v = r.lo; v < r.hi && w < cap; v++) ids[w++] = v;
+  if (n_written) *n_written = w;
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_workspace_size(const sf_plan* h, int64_t n, const sf_path_sel* sel, size_t* bytes) {
+  SF_GUARD_BEGIN
+  if (!h || !sel || !bytes) sf::fail(SF_EINVAL, "null argument");
+  if (n < 0) sf::fail(SF_EINVAL, "negative bitstring count");
+  ensure_device(*const_cast<sf::Plan*>(h->p));
+  *bytes = sf::exec_workspace_bytes(*h->p, n, *sel);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_amplitudes_device(sf_plan* h, const uint64_t* d_bits, int64_t n, const sf_path_sel* sel,
+                         double* d_out, int accumulate, void* d_ws, size_t ws_bytes, void* stream) {
+  SF_GUARD_BEGIN
+  if (!h || !sel) sf::fail(SF_EINVAL, "null argument");
+  if (n < 0) sf::fail(SF_EINVAL, "negative bitstring count");
+  if (n > 0 && (!d_bits || !d_out)) sf::fail(SF_EINVAL, "null device buffer");
+  ensure_device(*h->p);
+  sf::exec_run(*h->p, d_bits, n, *sel, d_out, accumulate, d_ws, ws_bytes, stream, true);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_amplitudes(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel* sel, double* out,
+                  double* f_actual) {
+  SF_GUARD_BEGIN
+  if (!h || !sel) sf::fail(SF_EINVAL, "null argument");
+  if (n < 0) sf::fail(SF_EINVAL, "negative bitstring count");
+  if (n > 0 && (!bits || !out)) sf::fail(SF_EINVAL, "null host buffer");
+  double fa = 0;
+  auto rs = sf::select_ranges(*h->p, *sel, &fa);
+  if (f_actual) *f_actual = fa;
+  if (n == 0) return SF_OK;
+  HostBuffers& hb = h->hb;
+  ensure_device(*h->p);
+  size_t need = sf::exec_workspace_bytes(*h->p, n, *sel);
+  if (!hb.stream) cuda_check(cudaStreamCreateWithFlags(&hb.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (hb.ws_bytes < need) {
+    if (hb.ws) cudaFree(hb.ws);
+    hb.ws = nullptr;
+    hb.ws_bytes = 0;
+    cuda_check(cudaMalloc(&hb.ws, need), "cudaMalloc workspace");
+    hb.ws_bytes = need;
+  }
+  if (hb.cap_n < n) {
+    if (hb.bits) cudaFree(hb.bits);
+    if (hb.out) cudaFree(hb.out);
+    hb.bits = nullptr;
+    hb.out = nullptr;
+    hb.cap_n = 0;
+    cuda_check(cudaMalloc(&hb.bits, (size_t)n * 8), "cudaMalloc bitstrings");
+    cuda_check(cudaMalloc(&hb.out, (size_t)n * 16), "cudaMalloc output");
+    hb.cap_n = n;
+  }
+  cuda_check(cudaMemcpyAsync(hb.bits, bits, (size_t)n * 8, cudaMemcpyHostToDevice, hb.stream), "cudaMemcpyAsync");
+  sf::exec_run(*h->p, hb.bits, n, *sel, hb.out, 0, hb.ws, hb.ws_bytes, hb.stream, true);
+  cuda_check(cudaMemcpyAsync(out, hb.out, (size_t)n * 16, cudaMemcpyDeviceToHost, hb.stream), "cudaMemcpyAsync");
+  cuda_check(cudaStreamSynchronize(hb.stream), "cudaStreamSynchronize");
+  return SF_OK;
+  SF_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,436 @@
+// Executor: walks the selected paths as a tree (Section 2: a process owns a
+// path prefix, checkpoints its state and runs every suffix from it; here the
+// checkpoints are resident device buffers per tree depth), launches the fused
+// passes for all nodes of a depth together, and gathers the requested
+// amplitudes of each batch of finished paths into FP64 sums (Eq. 2 / Eq. 3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <unordered_map>
+
+#include "sf_internal.h"
+
+namespace sf {
+
+namespace {
+
+size_t node_bytes(const Plan& p) { return (((size_t)1 << p.A.m) + ((size_t)1 << p.B.m)) * 8; }
+
+struct Slot {
+  uint64_t id = ~0ull;
+  bool valid = false;
+  bool dead = false;
+  cd sa = 1.0, sb = 1.0;
+};
+
+struct Cache {
+  const void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int B = 0;
+  std::vector<int> cap;                    // per cached depth
+  std::vector<size_t> first_slot;          // per cached depth
+  std::vector<std::vector<Slot>> slots;    // per cached depth
+  size_t final_first = 0;
+};
+
+struct Final {
+  uint64_t fid;
+  bool all;
+  uint64_t mask[4];
+};
+
+int total_bits_below(const Plan& p, int depth) {  // bits of levels[depth .. nL-1]
+  int b = 0;
+  for (size_t l = depth; l < p.levels.size(); l++) b += p.levels[l].bits;
+  return b;
+}
+
+// The block size (finals per block) and per-depth slot capacities.
+struct Layout {
+  int B = 1;
+  std::vector<int> cap;
+  size_t total_slots = 0;
+};
+
+Layout make_layout(const Plan& p, uint64_t n_finals) {
+  const int nL = (int)p.levels.size();
+  const size_t nb = node_bytes(p);
+  int64_t budget = p.opts.hbm_budget_bytes;
+  const size_t amps = ((size_t)1 << p.A.m) + ((size_t)1 << p.B.m);
+  int64_t B = p.opts.batch_paths > 0 ? p.opts.batch_paths : std::max<int64_t>(1, ((int64_t)1 << 26) / (int64_t)amps);
+  B = std::min<int64_t>(B, std::max<uint64_t>(1, n_finals));
+  Layout lay;
+  while (true) {
+    lay.cap.assign(std::max(0, nL), 0);
+    size_t tot = (size_t)B;
+    int cum = 0;
+    for (int s = 0; s < nL; s++) {
+      int64_t c = (cum >= 62) ? B : std::min<int64_t>(B, (int64_t)1 << cum);
+      lay.cap[s] = (int)c;
+      tot += (size_t)c;
+      if (s < nL) cum += p.levels[s].bits;
+    }
+    if ((int64_t)(tot * nb) <= budget || B == 1) {
+      lay.B = (int)B;
+      lay.total_slots = tot;
+      if ((int64_t)(tot * nb) > budget)
+        fail(SF_ENOMEM, "device memory budget too small for one path (" + std::to_string(tot * nb) +
+                            " bytes needed)");
+      return lay;
+    }
+    B = std::max<int64_t>(1, B / 2);
+  }
+}
+
+uint64_t count_finals(const Plan& p, const std::vector<Range>& rs) {
+  const int fb = p.deferred ? p.defer_bits : 0;
+  uint64_t n = 0, last = ~0ull;
+  for (auto& r : rs) {
+    uint64_t a = r.lo >> fb, b = (r.hi - 1) >> fb;
+    n += b - a + 1;
+    if (a == last) n--;
+    last = b;
+  }
+  return n;
+}
+
+void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan) {
+  if (pp.stages.size() > (size_t)MAX_STAGES || pp.ops.size() > (size_t)MAX_OPS ||
+      pp.phases.size() > (size_t)MAX_PHASE_GROUPS || pp.mats.size() > (size_t)2 * MAX_MATS)
+    fail(SF_EUNSUPPORTED, "internal: pass program too large");
+  L.pass = pp.dev;
+  std::copy(pp.stages.begin(), pp.stages.end(), L.stages);
+  std::copy(pp.ops.begin(), pp.ops.end(), L.ops);
+  std::copy(pp.phases.begin(), pp.phases.end(), L.phases);
+  std::copy(pp.mats.begin(), pp.mats.end(), L.mats);
+  for (size_t i = 0; i < plan.cross.size(); i++) {
+    L.xshift[i] = (uint8_t)plan.cross[i].shift;
+    L.xbits[i] = (uint8_t)plan.cross[i].bits;
+  }
+}
+
+int resolve(const Pin& pin, const Plan& p, uint64_t path) {
+  if (pin.xi < 0) return pin.v[0];
+  const CrossGate& x = p.cross[pin.xi];
+  int d = (int)((path >> x.shift) & ((1u << x.bits) - 1));
+  return pin.v[d];
+}
+
+bool dead_by_pins(const DevPass& dp, const Plan& p, uint64_t path) {
+  for (int i = 0; i < dp.n_pin_in; i++)
+    for (int j = i + 1; j < dp.n_pin_in; j++)
+      if (dp.pin_in[i].pos == dp.pin_in[j].pos) {
+        Pin a{dp.pin_in[i].pos, dp.pin_in[i].xi, {dp.pin_in[i].v[0], dp.pin_in[i].v[1], dp.pin_in[i].v[2], dp.pin_in[i].v[3]}};
+        Pin b{dp.pin_in[j].pos, dp.pin_in[j].xi, {dp.pin_in[j].v[0], dp.pin_in[j].v[1], dp.pin_in[j].v[2], dp.pin_in[j].v[3]}};
+        if (resolve(a, p, path) != resolve(b, p, path)) return true;
+      }
+  return false;
+}
+
+struct Job {
+  const void* in;  // parent buffer (half base) or nullptr for generated input
+  void* out;
+  uint64_t path;
+};
+
+// Run a segment program for a batch of nodes of one half.
+void run_segment(Cache&, const Plan& plan, const SegmentPlan& seg, const std::vector<Job>& jobs,
+                 cudaStream_t st) {
+  if (jobs.empty()) return;
+  for (size_t p = 0; p < seg.passes.size(); p++) {
+    const PassPlan& pp = seg.passes[p];
+    static thread_local std::unique_ptr<PassLaunch> scratch;
+    if (!scratch) {
+      scratch = std::make_unique<PassLaunch>();
+      std::memset(scratch.get(), 0, sizeof(PassLaunch));
+    }
+    PassLaunch* L = scratch.get();
+    fill_launch(*L, pp, plan);
+    const int tiles = 1 << pp.dev.n_free;
+    for (size_t j0 = 0; j0 < jobs.size(); j0 += MAX_NODES) {
+      size_t j1 = std::min(jobs.size(), j0 + MAX_NODES);
+      L->n_nodes = (int)(j1 - j0);
+      for (size_t j = j0; j < j1; j++) {
+        L->nodes[j - j0].in = (p == 0) ? jobs[j].in : jobs[j].out;
+        L->nodes[j - j0].out = jobs[j].out;
+        L->nodes[j - j0].path = jobs[j].path;
+      }
+      launch_pass(*L, tiles, plan.fuse_bits, plan.tile_bits, st);
+    }
+  }
+}
+
+}  // namespace
+
+size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s) {
+  (void)n;
+  double fa;
+  auto rs = select_ranges(p, s, &fa);
+  Layout lay = make_layout(p, count_finals(p, rs));
+  return lay.total_slots * node_bytes(p) + 256;
+}
+
+void exec_release_cache(Plan& p) {
+  delete reinterpret_cast<Cache*>(p.cache);
+  p.cache = nullptr;
+}
+
+void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& sel, double* d_out,
+              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache) {
+  cudaStream_t st = (cudaStream_t)stream;
+  double fa = 0;
+  std::vector<Range> rs = select_ranges(plan, sel, &fa);
+  if (n < 0) fail(SF_EINVAL, "negative bitstring count");
+  if (!accumulate) launch_zero(d_out, 2 * n, st);
+  if (n == 0 || rs.empty()) return;
+  const uint64_t nfin = count_finals(plan, rs);
+  Layout lay = make_layout(plan, nfin);
+  const size_t nb = node_bytes(plan);
+  const size_t need = lay.total_slots * nb + 256;
+  if (!ws || ws_bytes < need)
+    fail(SF_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~(uintptr_t)255);
+
+  Cache* C = reinterpret_cast<Cache*>(plan.cache);
+  if (!C || !keep_cache || C->ws != ws || C->ws_bytes != ws_bytes || C->B != lay.B || C->cap != lay.cap) {
+    delete C;
+    C = new Cache();
+    plan.cache = C;
+    C->ws = ws;
+    C->ws_bytes = ws_bytes;
+    C->B = lay.B;
+    C->cap = lay.cap;
+    size_t at = 0;
+    for (size_t s = 0; s < lay.cap.size(); s++) {
+      C->first_slot.push_back(at);
+      C->slots.emplace_back(lay.cap[s]);
+      at += lay.cap[s];
+    }
+    C->final_first = at;
+  }
+  const int nL = (int)plan.levels.size();
+  const size_t bytesA = ((size_t)1 << plan.A.m) * 8;
+  auto bufA = [&](size_t slot) { return (void*)(base + slot * nb); };
+  auto bufB = [&](size_t slot) { return (void*)(base + slot * nb + bytesA); };
+  const int fb = plan.deferred ? plan.defer_bits : 0;
+  const int sh_f = plan.deferred ? 0 : (nL > 0 ? plan.levels[nL - 1].bits : 0);
+  const SegmentPlan& finA = plan.deferred ? plan.A.last_deferred : plan.A.seg[nL];
+  const SegmentPlan& finB = plan.deferred ? plan.B.last_deferred : plan.B.seg[nL];
+
+  // gather template
+  GatherLaunch G;
+  std::memset(&G, 0, sizeof(G));
+  G.tabA = plan.d_tabA;
+  G.tabB = plan.d_tabB;
+  G.bits = d_bits;
+  G.acc = d_out;
+  G.n = n;
+  G.accumulate = 1;
+  G.g = plan.deferred ? plan.levels.back().n_cross : 0;
+  G.nterm_bits = plan.deferred ? plan.cross[plan.levels.back().first_cross].bits : 0;
+  for (int side = 0; side < 2; side++) {
+    const SegmentPlan& fin = side ? finB : finA;
+    const HalfPlan& H = side ? plan.B : plan.A;
+    GatherSide& gs = side ? G.B : G.A;
+    if (fin.pins_out.size() > (size_t)MAX_PINS) fail(SF_EUNSUPPORTED, "too many pins at gather");
+    gs.npin = (int)fin.pins_out.size();
+    for (size_t i = 0; i < fin.pins_out.size(); i++) {
+      const Pin& pn = fin.pins_out[i];
+      gs.pin[i].pos = (int8_t)pn.pos;
+      gs.pin[i].xi = (int8_t)pn.xi;
+      for (int t = 0; t < 4; t++) gs.pin[i].v[t] = (uint8_t)pn.v[t];
+    }
+    for (int t = 0; t < G.g; t++) {
+      const CrossGate& x = plan.cross[plan.levels.back().first_cross + t];
+      int q = side ? x.qb : x.qa;
+      gs.dpos[t] = (int8_t)H.pos_of[q];
+      gs.dq[t] = (int8_t)q;
+    }
+  }
+  std::memcpy(G.ma, plan.ma, sizeof(G.ma));
+  std::memcpy(G.mb, plan.mb, sizeof(G.mb));
+  for (size_t i = 0; i < plan.cross.size(); i++) {
+    G.xshift[i] = (uint8_t)plan.cross[i].shift;
+    G.xbits[i] = (uint8_t)plan.cross[i].bits;
+  }
+
+  // enumerate finals in order
+  std::vector<Final> block;
+  size_t ri = 0;
+  uint64_t cur = rs.empty() ? 0 : (rs[0].lo >> fb);
+  auto next_final = [&](Final& f) -> bool {
+    while (ri < rs.size()) {
+      const uint64_t lo = rs[ri].lo, hi = rs[ri].hi;
+      const uint64_t a = lo >> fb, b = (hi - 1) >> fb;
+      if (cur < a) cur = a;
+      if (cur > b) {
+        ri++;
+        continue;
+      }
+      f.fid = cur;
+      f.all = true;
+      std::memset(f.mask, 0, sizeof(f.mask));
+      if (fb > 0) {
+        const uint64_t glo = cur << fb, ghi = (cur + 1) << fb;
+        uint64_t cnt = 0;
+        // collect leaves of this final from every range that touches it
+        for (size_t r2 = ri; r2 < rs.size() && rs[r2].lo < ghi; r2++) {
+          uint64_t l = std::max(rs[r2].lo, glo), h = std::min(rs[r2].hi, ghi);
+          for (uint64_t v = l; v < h; v++) {
+            uint64_t b2 = v - glo;
+            f.mask[b2 >> 6] |= 1ull << (b2 & 63);
+            cnt++;
+          }
+        }
+        f.all = cnt == (1ull << fb);
+      }
+      cur++;
+      return true;
+    }
+    return false;
+  };
+
+  try {
+    Final f;
+    bool more = next_final(f);
+    while (more) {
+      block.clear();
+      while (more && (int)block.size() < lay.B) {
+        block.push_back(f);
+        more = next_final(f);
+      }
+      // parents at depth nL-1 (ids) of the block's finals
+      std::vector<uint64_t> pid(block.size());
+      for (size_t i = 0; i < block.size(); i++) pid[i] = block[i].fid >> sh_f;
+      // cached depths 0 .. nL-1
+      std::vector<size_t> slot_of_final_parent(block.size(), 0);
+      std::vector<int> prev_slot;  // slot index (within depth) per needed node at depth s-1
+      std::vector<uint64_t> prev_ids;
+      for (int s = 0; s < nL; s++) {
+        const int below = total_bits_below(plan, s) - (nL > 0 ? plan.levels[nL - 1].bits : 0);
+        // node id at depth s = pid >> (bits of levels s .. nL-2)
+        std::vector<uint64_t> ids;
+        for (uint64_t v : pid) {
+          uint64_t id = below >= 64 ? 0 : (v >> below);
+          if (ids.empty() || ids.back() != id) ids.push_back(id);
+        }
+        auto& slots = C->slots[s];
+        std::vector<int> where(ids.size(), -1);
+        std::vector<bool> keep(slots.size(), false);
+        {
+          std::unordered_map<uint64_t, int> resident;
+          for (size_t q = 0; q < slots.size(); q++)
+            if (slots[q].valid) resident[slots[q].id] = (int)q;
+          for (size_t i = 0; i < ids.size(); i++) {
+            auto it = resident.find(ids[i]);
+            if (it != resident.end()) {
+              where[i] = it->second;
+              keep[it->second] = true;
+            }
+          }
+        }
+        size_t freep = 0;
+        std::vector<Job> jobsA, jobsB;
+        std::vector<size_t> computed;
+        for (size_t i = 0; i < ids.size(); i++) {
+          if (where[i] >= 0) continue;
+          while (freep < slots.size() && keep[freep]) freep++;
+          if (freep >= slots.size()) fail(SF_EINVAL, "internal: slot capacity");
+          where[i] = (int)freep;
+          keep[freep] = true;
+          Slot& sl = slots[freep];
+          sl.id = ids[i];
+          sl.valid = false;
+          const uint64_t path = (total_bits_below(plan, s) >= 64) ? 0 : (ids[i] << total_bits_below(plan, s));
+          // parent
+          const void *inA = nullptr, *inB = nullptr;
+          bool pdead = false;
+          cd psa = plan.A.root_scale, psb = plan.B.root_scale;
+          if (s > 0) {
+            const uint64_t parent = ids[i] >> plan.levels[s - 1].bits;
+            size_t pi = std::lower_bound(prev_ids.begin(), prev_ids.end(), parent) - prev_ids.begin();
+            if (pi >= prev_ids.size() || prev_ids[pi] != parent) fail(SF_EINVAL, "internal: parent missing");
+            const Slot& ps = C->slots[s - 1][prev_slot[pi]];
+            pdead = ps.dead;
+            psa = ps.sa;
+            psb = ps.sb;
+            inA = bufA(C->first_slot[s - 1] + prev_slot[pi]);
+            inB = bufB(C->first_slot[s - 1] + prev_slot[pi]);
+          }
+          const SegmentPlan& sA = plan.A.seg[s];
+          const SegmentPlan& sB = plan.B.seg[s];
+          sl.dead = pdead || dead_by_pins(sA.passes[0].dev, plan, path) || dead_by_pins(sB.passes[0].dev, plan, path);
+          sl.sa = psa * sA.scale;
+          sl.sb = psb * sB.scale;
+          if (!sl.dead) {
+            jobsA.push_back({inA, bufA(C->first_slot[s] + freep), path});
+            jobsB.push_back({inB, bufB(C->first_slot[s] + freep), path});
+          }
+          computed.push_back(freep);
+        }
+        run_segment(*C, plan, plan.A.seg[s], jobsA, st);
+        run_segment(*C, plan, plan.B.seg[s], jobsB, st);
+        for (size_t q : computed) slots[q].valid = true;
+        prev_ids = ids;
+        prev_slot = where;
+      }
+      // finals
+      std::vector<Job> jobsA, jobsB;
+      std::vector<GatherFinal> gf;
+      for (size_t i = 0; i < block.size(); i++) {
+        const uint64_t fpath = block[i].fid << fb;
+        const void *inA = nullptr, *inB = nullptr;
+        bool pdead = false;
+        cd psa = plan.A.root_scale, psb = plan.B.root_scale;
+        if (nL > 0) {
+          size_t pi = std::lower_bound(prev_ids.begin(), prev_ids.end(), pid[i]) - prev_ids.begin();
+          if (pi >= prev_ids.size() || prev_ids[pi] != pid[i]) fail(SF_EINVAL, "internal: final parent missing");
+          const Slot& ps = C->slots[nL - 1][prev_slot[pi]];
+          pdead = ps.dead;
+          psa = ps.sa;
+          psb = ps.sb;
+          inA = bufA(C->first_slot[nL - 1] + prev_slot[pi]);
+          inB = bufB(C->first_slot[nL - 1] + prev_slot[pi]);
+        }
+        bool dead = pdead || dead_by_pins(finA.passes[0].dev, plan, fpath) ||
+                    dead_by_pins(finB.passes[0].dev, plan, fpath);
+        if (dead) continue;
+        const size_t fs = C->final_first + i;
+        jobsA.push_back({inA, bufA(fs), fpath});
+        jobsB.push_back({inB, bufB(fs), fpath});
+        GatherFinal g;
+        std::memset(&g, 0, sizeof(g));
+        g.wa = bufA(fs);
+        g.wb = bufB(fs);
+        g.path = fpath;
+        cd sc = psa * finA.scale * psb * finB.scale;
+        g.sre = sc.real();
+        g.sim = sc.imag();
+        g.all_leaves = block[i].all ? 1 : 0;
+        std::memcpy(g.leafmask, block[i].mask, sizeof(g.leafmask));
+        gf.push_back(g);
+      }
+      run_segment(*C, plan, finA, jobsA, st);
+      run_segment(*C, plan, finB, jobsB, st);
+      for (size_t g0 = 0; g0 < gf.size(); g0 += GATHER_FINALS) {
+        size_t g1 = std::min(gf.size(), g0 + GATHER_FINALS);
+        G.n_finals = (int)(g1 - g0);
+        for (size_t j = g0; j < g1; j++) G.finals[j - g0] = gf[j];
+        launch_gather(G, st);
+      }
+    }
+  } catch (...) {
+    for (auto& v : C->slots)
+      for (auto& sl : v) sl.valid = false;
+    throw;
+  }
+  if (!keep_cache) {
+    for (auto& v : C->slots)
+      for (auto& sl : v) sl.valid = false;
+  }
+}
+
+}  // namespace sf

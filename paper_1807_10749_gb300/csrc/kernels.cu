@@ -1,0 +1,633 @@
+// Device kernels of the Schroedinger-Feynman path sum (arXiv:1807.10749).
+//
+//  pass_kernel   - one fused pass over a half-state: each CTA owns a tile of
+//                  2^k amplitudes (the low L index bits plus k-L chosen higher
+//                  bits), stages it in shared memory, and runs a sequence of
+//                  register stages; a stage gives every thread 2^R amplitudes
+//                  whose R "register bits" vary, applies the stage's gates in
+//                  registers, and writes them back. Gates: the Google gates in
+//                  their multiplication-free integer form (Section 2: "no
+//                  floating-point multiplications except for T"), general 2x2
+//                  and 4x4 matrices, per-path cross-gate factors (Eq. 1 and
+//                  Section 7), and groups of diagonal gates applied as one
+//                  mod-8 power of e^{i pi/4} computed from bitmasks (Section 2:
+//                  parity / popcount and mod-8 arithmetic). Projections are
+//                  never executed: the zero half of a projected qubit is not
+//                  read or written (Section 2: zero-block skipping).
+//  gather_kernel - for each requested bitstring x, the product of the two
+//                  halves' amplitudes at (x_A, x_B) summed over a batch of
+//                  paths (Eq. 2), with the last branch level contracted in
+//                  closed form when the planner deferred it; FP64 accumulation.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "sf_internal.h"
+
+namespace sf {
+
+namespace {
+
+__device__ __forceinline__ int digit_of(const uint8_t* xshift, const uint8_t* xbits, uint64_t path,
+                                        int xi) {
+  return (int)((path >> xshift[xi]) & ((1u << xbits[xi]) - 1u));
+}
+
+// count of trailing zeros, folded at compile time for unrolled loop indices
+__host__ __device__ constexpr int cctz(int v) {
+  int r = 0;
+  while (v && !(v & 1)) {
+    v >>= 1;
+    r++;
+  }
+  return r;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+
+// ---- register-block gate kernels (J = register bit, compile time) --------
+template <int R, int J>
+__device__ __forceinline__ void g_h(float2* v) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    v[i] = make_float2(a.x + b.x, a.y + b.y);
+    v[i | (1 << J)] = make_float2(a.x - b.x, a.y - b.y);
+  }
+}
+// 2 X^1/2 = [[1+i, 1-i], [1-i, 1+i]]: out0 = s + i d, out1 = s - i d
+template <int R, int J>
+__device__ __forceinline__ void g_xh(float2* v) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
+    v[i] = make_float2(sx - dy, sy + dx);
+    v[i | (1 << J)] = make_float2(sx + dy, sy - dx);
+  }
+}
+// 2 Y^1/2 = [[1+i, -1-i], [1+i, 1+i]]: out0 = (1+i)(a-b), out1 = (1+i)(a+b)
+template <int R, int J>
+__device__ __forceinline__ void g_yh(float2* v) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
+    v[i] = make_float2(dx - dy, dx + dy);
+    v[i | (1 << J)] = make_float2(sx - sy, sx + sy);
+  }
+}
+template <int R, int J>
+__device__ __forceinline__ void g_1(float2* v, float2 m0, float2 m1, float2 m2, float2 m3) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    v[i] = cadd(cmul(m0, a), cmul(m1, b));
+    v[i | (1 << J)] = cadd(cmul(m2, a), cmul(m3, b));
+  }
+}
+template <int R, int J>
+__device__ __forceinline__ void g_dmul(float2* v, float2 f0, float2 f1) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) v[i] = cmul((i & (1 << J)) ? f1 : f0, v[i]);
+}
+// 4x4 on register bits (A = high basis bit, B = low basis bit)
+template <int R, int A, int B>
+__device__ __forceinline__ void g_2(float2* v, const float* m) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & ((1 << A) | (1 << B))) continue;
+    const int i0 = i, i1 = i | (1 << B), i2 = i | (1 << A), i3 = i | (1 << A) | (1 << B);
+    float2 x[4] = {v[i0], v[i1], v[i2], v[i3]};
+    float2 y[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        float2 mm = make_float2(m[2 * (4 * r + c)], m[2 * (4 * r + c) + 1]);
+        acc = cadd(acc, cmul(mm, x[c]));
+      }
+      y[r] = acc;
+    }
+    v[i0] = y[0];
+    v[i1] = y[1];
+    v[i2] = y[2];
+    v[i3] = y[3];
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void dispatch_1q(int code, int a, float2* v) {
+#define SF_CASE(J)                                    \
+  case J:                                             \
+    if constexpr (J < R) {                            \
+      if (code == DOP_H) g_h<R, J>(v);                \
+      else if (code == DOP_XH) g_xh<R, J>(v);         \
+      else g_yh<R, J>(v);                             \
+    }                                                 \
+    break;
+  switch (a) { SF_CASE(0) SF_CASE(1) SF_CASE(2) SF_CASE(3) SF_CASE(4) }
+#undef SF_CASE
+}
+
+template <int R>
+__device__ __forceinline__ void dispatch_g1(int a, float2* v, float2 m0, float2 m1, float2 m2, float2 m3) {
+#define SF_CASE(J) \
+  case J:          \
+    if constexpr (J < R) g_1<R, J>(v, m0, m1, m2, m3); \
+    break;
+  switch (a) { SF_CASE(0) SF_CASE(1) SF_CASE(2) SF_CASE(3) SF_CASE(4) }
+#undef SF_CASE
+}
+
+template <int R>
+__device__ __forceinline__ void dispatch_dmul(int a, float2* v, float2 f0, float2 f1) {
+#define SF_CASE(J) \
+  case J:          \
+    if constexpr (J < R) g_dmul<R, J>(v, f0, f1); \
+    break;
+  switch (a) { SF_CASE(0) SF_CASE(1) SF_CASE(2) SF_CASE(3) SF_CASE(4) }
+#undef SF_CASE
+}
+
+template <int R>
+__device__ __forceinline__ void dispatch_g2(int a, int b, float2* v, const float* m) {
+#define SF_C2(A, B)                                                          \
+  case (A * 8 + B):                                                          \
+    if constexpr (A < R && B < R && A != B) g_2<R, A, B>(v, m); \
+    break;
+#define SF_ROW(A) SF_C2(A, 0) SF_C2(A, 1) SF_C2(A, 2) SF_C2(A, 3) SF_C2(A, 4)
+  switch (a * 8 + b) { SF_ROW(0) SF_ROW(1) SF_ROW(2) SF_ROW(3) SF_ROW(4) }
+#undef SF_ROW
+#undef SF_C2
+}
+
+// Phase group on a register block. gfix: global index of the thread's fixed
+// bits; gr[j]: global position of register bit j. k(i) is a quadratic form in
+// the register bits, evaluated in Gray-code order (one update per amplitude).
+template <int R>
+__device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* v, uint32_t gfix,
+                                            const int* gr, const uint8_t* xshift, const uint8_t* xbits,
+                                            uint64_t path, const float2* w8) {
+  int k0 = __popc(gfix & g.m1) + 2 * __popc(gfix & g.m2) + 4 * __popc(gfix & g.m4);
+  int w[R];
+  uint32_t q[R];
+  uint32_t rmask = 0;
+#pragma unroll
+  for (int j = 0; j < R; j++) {
+    const int p = gr[j];
+    w[j] = (int)((g.m1 >> p) & 1u) + 2 * (int)((g.m2 >> p) & 1u) + 4 * (int)((g.m4 >> p) & 1u);
+    q[j] = 0;
+    rmask |= 1u << p;
+  }
+  for (int c = 0; c < g.ncz; c++) {
+    const int p0 = g.cz[c][0], p1 = g.cz[c][1];
+    const bool r0 = (rmask >> p0) & 1u, r1 = (rmask >> p1) & 1u;
+    if (!r0 && !r1) {
+      k0 += 4 * (int)((gfix >> p0) & (gfix >> p1) & 1u);
+    } else {
+#pragma unroll
+      for (int j = 0; j < R; j++) {
+        if (r0 && r1) {
+          if (gr[j] == p0) {
+#pragma unroll
+            for (int l = 0; l < R; l++)
+              if (gr[l] == p1) q[j] |= 1u << l;
+          } else if (gr[j] == p1) {
+#pragma unroll
+            for (int l = 0; l < R; l++)
+              if (gr[l] == p0) q[j] |= 1u << l;
+          }
+        } else if (r0 && gr[j] == p0) {
+          w[j] += 4 * (int)((gfix >> p1) & 1u);
+        } else if (r1 && gr[j] == p1) {
+          w[j] += 4 * (int)((gfix >> p0) & 1u);
+        }
+      }
+    }
+  }
+  for (int s = 0; s < g.nsel; s++) {
+    const int p = g.sel[s].pos;
+    const int d = g.sel[s].xi >= 0 ? digit_of(xshift, xbits, path, g.sel[s].xi) : 0;
+    const int ws = g.sel[s].w[d];
+    if ((rmask >> p) & 1u) {
+#pragma unroll
+      for (int j = 0; j < R; j++)
+        if (gr[j] == p) w[j] += ws;
+    } else {
+      k0 += ws * (int)((gfix >> p) & 1u);
+    }
+  }
+  int kk = k0;
+  v[0] = cmul(v[0], w8[kk & 7]);
+#pragma unroll
+  for (int i = 1; i < (1 << R); i++) {
+    const int gi = i ^ (i >> 1);
+    const int prev = (i - 1) ^ ((i - 1) >> 1);
+    const int j = cctz(gi ^ prev);  // flipped bit (compile time)
+    const int rest = gi & ~(1 << j);
+    const int delta = w[j] + 4 * __popc(q[j] & (uint32_t)rest);
+    if (gi & (1 << j)) kk += delta;
+    else kk -= delta;
+    v[gi] = cmul(v[gi], w8[kk & 7]);
+  }
+}
+
+__device__ __forceinline__ uint32_t pin_val(const DevPin& p, const uint8_t* xshift, const uint8_t* xbits,
+                                            uint64_t path) {
+  return p.xi < 0 ? p.v[0] : p.v[digit_of(xshift, xbits, path, p.xi)];
+}
+
+}  // namespace
+
+template <int R>
+__global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PassLaunch P) {
+  extern __shared__ float4 smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  const DevPass& d = P.pass;
+  const int k = d.k, L = d.L;
+  const int ntile = 1 << k;
+  uint32_t* runoff = reinterpret_cast<uint32_t*>(sm + ntile);
+  __shared__ float2 w8[8];
+  const int node = blockIdx.y;
+  const uint64_t path = P.nodes[node].path;
+
+  uint32_t base = 0;
+  {
+    const uint32_t t = blockIdx.x;
+    for (int i = 0; i < d.n_free; i++) base |= ((t >> i) & 1u) << d.freepos[i];
+  }
+  uint32_t active = 0;
+  for (int j = 0; j < k; j++) active |= 1u << d.gpos[j];
+  uint32_t pin_mask = 0, pin_val_g = 0;
+  for (int i = 0; i < d.n_pin_in; i++) {
+    const uint32_t b = 1u << d.pin_in[i].pos;
+    pin_mask |= b;
+    if (pin_val(d.pin_in[i], P.xshift, P.xbits, path)) pin_val_g |= b;
+  }
+  uint32_t pout_mask = 0, pout_val = 0;
+  for (int i = 0; i < d.n_pin_out; i++) {
+    const uint32_t b = 1u << d.pin_out[i].pos;
+    pout_mask |= b;
+    if (pin_val(d.pin_out[i], P.xshift, P.xbits, path)) pout_val |= b;
+  }
+  base |= pin_val_g & ~active;
+  uint32_t lin_m = 0, lin_v = 0, lout_m = 0, lout_v = 0;
+  for (int j = 0; j < k; j++) {
+    const uint32_t gb = 1u << d.gpos[j];
+    if (pin_mask & gb) {
+      lin_m |= 1u << j;
+      if (pin_val_g & gb) lin_v |= 1u << j;
+    }
+    if (pout_mask & gb) {
+      lout_m |= 1u << j;
+      if (pout_val & gb) lout_v |= 1u << j;
+    }
+  }
+  if (threadIdx.x < 8) {
+    const float r = 0.70710678118654752f;
+    const float2 t8[8] = {{1.f, 0.f}, {r, r}, {0.f, 1.f}, {-r, r}, {-1.f, 0.f}, {-r, -r}, {0.f, -1.f}, {r, -r}};
+    w8[threadIdx.x] = t8[threadIdx.x];
+  }
+  const int nruns = 1 << (k - L);
+  for (int rI = threadIdx.x; rI < nruns; rI += blockDim.x) {
+    uint32_t hi = 0;
+    for (int j = L; j < k; j++) hi |= (uint32_t)((rI >> (j - L)) & 1) << d.gpos[j];
+    runoff[rI] = hi;
+  }
+  __syncthreads();
+
+  // ---- load the tile (global -> shared), zero outside the input pins ----
+  const float2* in = reinterpret_cast<const float2*>(P.nodes[node].in);
+  const int lmask = (1 << L) - 1;
+  for (int e = threadIdx.x; e < ntile; e += blockDim.x) {
+    const int off = e & lmask;
+    const uint32_t g = base | runoff[e >> L] | (uint32_t)off;
+    float2 val = make_float2(0.f, 0.f);
+    if (((uint32_t)e & lin_m) == lin_v) val = d.gen_input ? make_float2(1.f, 0.f) : in[g];
+    sm[e] = val;
+  }
+  __syncthreads();
+
+  // ---- register stages ----
+  for (int s = 0; s < d.n_stages; s++) {
+    const DevStage& st = P.stages[s];
+    int roff[R], gr[R];
+    uint32_t rl = 0;
+#pragma unroll
+    for (int j = 0; j < R; j++) {
+      roff[j] = 1 << st.rbit[j];
+      gr[j] = d.gpos[st.rbit[j]];
+      rl |= 1u << st.rbit[j];
+    }
+    // thread's fixed local bits: threadIdx bits deposited into non-register bits
+    uint32_t lfix = 0;
+    {
+      uint32_t t = threadIdx.x;
+      for (int j = 0; j < k; j++) {
+        if ((rl >> j) & 1u) continue;
+        lfix |= (t & 1u) << j;
+        t >>= 1;
+      }
+    }
+    uint32_t gfix = base;
+    for (int j = 0; j < k; j++)
+      if ((lfix >> j) & 1u) gfix |= 1u << d.gpos[j];
+    float2 v[1 << R];
+    {
+      int addr = (int)lfix;
+      v[0] = sm[addr];
+#pragma unroll
+      for (int i = 1; i < (1 << R); i++) {
+        const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
+        const int j = cctz(gi ^ prev);
+        addr += (gi & (1 << j)) ? roff[j] : -roff[j];
+        v[gi] = sm[addr];
+      }
+    }
+    for (int o = st.op_begin; o < st.op_end; o++) {
+      const DevOp& op = P.ops[o];
+      switch (op.code) {
+        case DOP_H:
+        case DOP_XH:
+        case DOP_YH:
+          dispatch_1q<R>(op.code, op.a, v);
+          break;
+        case DOP_G1: {
+          const float* m = P.mats + 2 * op.arg;
+          dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                         make_float2(m[4], m[5]), make_float2(m[6], m[7]));
+          break;
+        }
+        case DOP_G1SEL: {
+          const int dg = digit_of(P.xshift, P.xbits, path, op.xi);
+          const float* m = P.mats + 2 * (op.arg + 4 * dg);
+          dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                         make_float2(m[4], m[5]), make_float2(m[6], m[7]));
+          break;
+        }
+        case DOP_G2:
+          dispatch_g2<R>(op.a, op.b, v, P.mats + 2 * op.arg);
+          break;
+        case DOP_PHASE:
+          apply_phase<R>(P.phases[op.arg], v, gfix, gr, P.xshift, P.xbits, path, w8);
+          break;
+        case DOP_DMUL: {
+          const float* m = P.mats + 2 * op.arg;
+          const float2 f0 = make_float2(m[0], m[1]), f1 = make_float2(m[2], m[3]);
+          int jr = -1;
+#pragma unroll
+          for (int j = 0; j < R; j++)
+            if (gr[j] == op.a) jr = j;
+          if (jr >= 0) {
+            dispatch_dmul<R>(jr, v, f0, f1);
+          } else {
+            const float2 f = ((gfix >> op.a) & 1u) ? f1 : f0;
+#pragma unroll
+            for (int i = 0; i < (1 << R); i++) v[i] = cmul(f, v[i]);
+          }
+          break;
+        }
+        default:
+          break;
+      }
+    }
+    {
+      int addr = (int)lfix;
+      sm[addr] = v[0];
+#pragma unroll
+      for (int i = 1; i < (1 << R); i++) {
+        const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
+        const int j = cctz(gi ^ prev);
+        addr += (gi & (1 << j)) ? roff[j] : -roff[j];
+        sm[addr] = v[gi];
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- store the tile (shared -> global), skipping pinned-out positions ----
+  float2* out = reinterpret_cast<float2*>(P.nodes[node].out);
+  const float sc = d.post_scale;
+  for (int e = threadIdx.x; e < ntile; e += blockDim.x) {
+    if (((uint32_t)e & lout_m) != lout_v) continue;
+    const int off = e & lmask;
+    const uint32_t g = base | runoff[e >> L] | (uint32_t)off;
+    float2 val = sm[e];
+    out[g] = make_float2(val.x * sc, val.y * sc);
+  }
+}
+
+// ------------------------------------------------------------------ gather
+template <int G>
+__global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherLaunch P) {
+  __shared__ uint32_t tA[8 * 256], tB[8 * 256];
+  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) {
+    tA[i] = P.tabA[i];
+    tB[i] = P.tabB[i];
+  }
+  __syncthreads();
+  const int NY = 1 << G;
+  const int tb = P.nterm_bits;
+  const int nt = 1 << tb;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t x = P.bits[i];
+    uint32_t ia = 0, ib = 0;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+      const uint32_t byte = (uint32_t)(x >> (8 * b)) & 255u;
+      ia |= tA[b * 256 + byte];
+      ib |= tB[b * 256 + byte];
+    }
+    int xa[G > 0 ? G : 1], xb[G > 0 ? G : 1];
+#pragma unroll
+    for (int t = 0; t < G; t++) {
+      xa[t] = (int)((x >> P.A.dq[t]) & 1u);
+      xb[t] = (int)((x >> P.B.dq[t]) & 1u);
+    }
+    double sr = 0.0, si = 0.0;
+    for (int f = 0; f < P.n_finals; f++) {
+      const GatherFinal& F = P.finals[f];
+      uint32_t pam = 0, pav = 0, pbm = 0, pbv = 0;
+      for (int p = 0; p < P.A.npin; p++) {
+        pam |= 1u << P.A.pin[p].pos;
+        if (pin_val(P.A.pin[p], P.xshift, P.xbits, F.path)) pav |= 1u << P.A.pin[p].pos;
+      }
+      for (int p = 0; p < P.B.npin; p++) {
+        pbm |= 1u << P.B.pin[p].pos;
+        if (pin_val(P.B.pin[p], P.xshift, P.xbits, F.path)) pbv |= 1u << P.B.pin[p].pos;
+      }
+      const float2* WA = reinterpret_cast<const float2*>(F.wa);
+      const float2* WB = reinterpret_cast<const float2*>(F.wb);
+      float2 wa[1 << G], wb[1 << G];
+#pragma unroll
+      for (int y = 0; y < NY; y++) {
+        uint32_t ja = ia, jb = ib;
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+          ja |= (uint32_t)((y >> t) & 1) << P.A.dpos[t];
+          jb |= (uint32_t)((y >> t) & 1) << P.B.dpos[t];
+        }
+        wa[y] = ((ja & pam) == pav) ? WA[ja] : make_float2(0.f, 0.f);
+        wb[y] = ((jb & pbm) == pbv) ? WB[jb] : make_float2(0.f, 0.f);
+      }
+      float2 c = make_float2(0.f, 0.f);
+      if (G == 0) {
+        c = cmul(wa[0], wb[0]);
+      } else if (F.all_leaves) {
+        // sum over every leaf: contract wb with K_t[y, z] = sum_d MA_{t,d}[xa_t, y] MB_{t,d}[xb_t, z]
+        float2 tv[1 << G];
+#pragma unroll
+        for (int z = 0; z < NY; z++) tv[z] = wb[z];
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+          float2 K[2][2];
+#pragma unroll
+          for (int y = 0; y < 2; y++)
+#pragma unroll
+            for (int z = 0; z < 2; z++) {
+              float2 acc = make_float2(0.f, 0.f);
+              for (int dd = 0; dd < nt; dd++) {
+                const float* ma = P.ma[t][dd];
+                const float* mb = P.mb[t][dd];
+                float2 a = make_float2(ma[2 * (2 * xa[t] + y)], ma[2 * (2 * xa[t] + y) + 1]);
+                float2 b = make_float2(mb[2 * (2 * xb[t] + z)], mb[2 * (2 * xb[t] + z) + 1]);
+                acc = cadd(acc, cmul(a, b));
+              }
+              K[y][z] = acc;
+            }
+#pragma unroll
+          for (int y = 0; y < NY; y++) {
+            if (y & (1 << t)) continue;
+            const float2 t0 = tv[y], t1 = tv[y | (1 << t)];
+            tv[y] = cadd(cmul(K[0][0], t0), cmul(K[0][1], t1));
+            tv[y | (1 << t)] = cadd(cmul(K[1][0], t0), cmul(K[1][1], t1));
+          }
+        }
+#pragma unroll
+        for (int y = 0; y < NY; y++) c = cadd(c, cmul(wa[y], tv[y]));
+      } else {
+        const int nleaf = 1 << (G * tb);
+        for (int b = 0; b < nleaf; b++) {
+          if (!((F.leafmask[b >> 6] >> (b & 63)) & 1ull)) continue;
+          float2 av = make_float2(0.f, 0.f), bv = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int y = 0; y < NY; y++) {
+            float2 ca = make_float2(1.f, 0.f), cb = make_float2(1.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < G; t++) {
+              const int dd = (b >> ((G - 1 - t) * tb)) & (nt - 1);
+              const int yt = (y >> t) & 1;
+              const float* ma = P.ma[t][dd];
+              const float* mb = P.mb[t][dd];
+              ca = cmul(ca, make_float2(ma[2 * (2 * xa[t] + yt)], ma[2 * (2 * xa[t] + yt) + 1]));
+              cb = cmul(cb, make_float2(mb[2 * (2 * xb[t] + yt)], mb[2 * (2 * xb[t] + yt) + 1]));
+            }
+            av = cadd(av, cmul(ca, wa[y]));
+            bv = cadd(bv, cmul(cb, wb[y]));
+          }
+          c = cadd(c, cmul(av, bv));
+        }
+      }
+      sr += (double)c.x * F.sre - (double)c.y * F.sim;
+      si += (double)c.x * F.sim + (double)c.y * F.sre;
+    }
+    if (P.accumulate) {
+      P.acc[2 * i] += sr;
+      P.acc[2 * i + 1] += si;
+    } else {
+      P.acc[2 * i] = sr;
+      P.acc[2 * i + 1] = si;
+    }
+  }
+}
+
+__global__ void zero_kernel(double* p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0.0;
+}
+
+// ------------------------------------------------------------- launchers
+static void check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(SF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+template <int R>
+static void launch_pass_r(const PassLaunch& L, int tiles, int tile_k, cudaStream_t s) {
+  const int threads = 1 << (tile_k - R);
+  const size_t smem = ((size_t)8 << tile_k) + ((size_t)4 << (tile_k - L.pass.L)) + 16;
+  static int configured[MAX_K + 1] = {0};
+  if (!configured[tile_k]) {
+    check(cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+          "cudaFuncSetAttribute");
+    configured[tile_k] = 1;
+  }
+  dim3 grid(tiles, L.n_nodes);
+  pass_kernel<R><<<grid, threads, smem, s>>>(L);
+  check(cudaGetLastError(), "pass_kernel launch");
+}
+
+void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = L.pass.k;
+  const int R = L.pass.R;
+  if (k - R > 9 || k > MAX_K || R < 1) fail(SF_EINVAL, "internal: bad tile shape");
+  (void)fuse_bits;
+  (void)tile_bits;
+  switch (R) {
+    case 1: launch_pass_r<1>(L, tiles, k, s); break;
+    case 2: launch_pass_r<2>(L, tiles, k, s); break;
+    case 3: launch_pass_r<3>(L, tiles, k, s); break;
+    case 4: launch_pass_r<4>(L, tiles, k, s); break;
+    case 5: launch_pass_r<5>(L, tiles, k, s); break;
+    default: fail(SF_EINVAL, "internal: bad register bits");
+  }
+}
+
+void launch_gather(const GatherLaunch& L, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (L.n <= 0) return;
+  const int threads = 256;
+  int64_t blocks = (L.n + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  switch (L.g) {
+    case 0: gather_kernel<0><<<(int)blocks, threads, 0, s>>>(L); break;
+    case 1: gather_kernel<1><<<(int)blocks, threads, 0, s>>>(L); break;
+    case 2: gather_kernel<2><<<(int)blocks, threads, 0, s>>>(L); break;
+    case 3: gather_kernel<3><<<(int)blocks, threads, 0, s>>>(L); break;
+    case 4: gather_kernel<4><<<(int)blocks, threads, 0, s>>>(L); break;
+    default: fail(SF_EINVAL, "internal: too many deferred gates");
+  }
+  check(cudaGetLastError(), "gather_kernel launch");
+}
+
+void launch_zero(double* p, int64_t n, void* stream) {
+  if (n <= 0) return;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  zero_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(p, n);
+  check(cudaGetLastError(), "zero_kernel launch");
+}
+
+}  // namespace sf

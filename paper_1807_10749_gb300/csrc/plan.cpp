@@ -1,0 +1,907 @@
+// Planner: cut, cross-gate decompositions, path-tree levels, per-half op
+// lists, and the fused pass / register-stage programs the kernels run.
+//
+// Paper correspondence:
+//   cut selection ........... Section 8 (one straight cut, minimise the larger
+//                             block, then the number of cross gates)
+//   cross-gate terms ........ Eq. 1 (CZ), Eq. 4way and the operator-Schmidt
+//                             decomposition (Sections 3 and 7)
+//   path tree levels ........ Section 2 (prefix/suffix split with checkpoints)
+//   zero-block skipping ..... Section 2 (projections leave blocks of zeros)
+//   gate clustering, bitmask
+//   diagonal passes, slices . Section 2 (clusters by kind; parity/popcount and
+//                             mod-8 arithmetic for diagonal gates; cache-sized
+//                             slices)
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+
+#include "sf_internal.h"
+
+namespace sf {
+
+namespace {
+
+const double kS2 = std::sqrt(0.5);
+
+bool near(cd a, cd b, double tol = 1e-14) { return std::abs(a - b) <= tol; }
+
+// e^{i pi w / 4} for w in 0..7
+cd omega(int w) {
+  static const double r = std::sqrt(0.5);
+  static const cd t[8] = {cd(1, 0), cd(r, r), cd(0, 1), cd(-r, r),
+                          cd(-1, 0), cd(-r, -r), cd(0, -1), cd(r, -r)};
+  return t[((w % 8) + 8) % 8];
+}
+
+// If z is a power of e^{i pi/4} return its exponent, else -1.
+int omega_exp(cd z) {
+  for (int w = 0; w < 8; w++)
+    if (near(z, omega(w), 1e-15)) return w;
+  return -1;
+}
+
+void mul2(const cd* a, const cd* b, cd* out) {  // out = a * b (2x2)
+  cd r[4];
+  r[0] = a[0] * b[0] + a[1] * b[2];
+  r[1] = a[0] * b[1] + a[1] * b[3];
+  r[2] = a[2] * b[0] + a[3] * b[2];
+  r[3] = a[2] * b[1] + a[3] * b[3];
+  for (int i = 0; i < 4; i++) out[i] = r[i];
+}
+
+// ----------------------------------------------------------- cut selection
+uint64_t auto_cut(const Circuit& c) {
+  uint64_t best = 0;
+  long best_big = 1 << 30, best_x = 1 << 30;
+  auto consider = [&](uint64_t mask) {
+    int nb = __builtin_popcountll(mask);
+    int big = std::max(nb, c.n - nb);
+    long x = 0;
+    for (auto& g : c.gates)
+      if (g.nq() == 2 && (((mask >> g.q0) ^ (mask >> g.q1)) & 1)) x++;
+    if (big < best_big || (big == best_big && x < best_x)) {
+      best = mask;
+      best_big = big;
+      best_x = x;
+    }
+  };
+  for (int cc = 1; cc < c.cols; cc++) {
+    uint64_t m = 0;
+    for (int r = 0; r < c.rows; r++)
+      for (int k = cc; k < c.cols; k++) m |= 1ull << (r * c.cols + k);
+    consider(m);
+  }
+  for (int rr = 1; rr < c.rows; rr++) {
+    uint64_t m = 0;
+    for (int r = rr; r < c.rows; r++)
+      for (int k = 0; k < c.cols; k++) m |= 1ull << (r * c.cols + k);
+    consider(m);
+  }
+  if (!best) fail(SF_EINVAL, "no straight cut exists for a 1-qubit grid");
+  return best;
+}
+
+// ---------------------------------------------------------- decompositions
+void decompose(const Gate& g, bool q0_on_a, int decomposition, CrossGate& x) {
+  const cd I(0, 1);
+  cd U[16];
+  for (int i = 0; i < 16; i++) U[i] = g.m[i];
+  if (!q0_on_a) {  // SWAP U SWAP: A-side qubit becomes the high basis bit
+    const int sw[4] = {0, 2, 1, 3};
+    cd V[16];
+    for (int r = 0; r < 4; r++)
+      for (int c = 0; c < 4; c++) V[4 * r + c] = U[4 * sw[r] + sw[c]];
+    for (int i = 0; i < 16; i++) U[i] = V[i];
+  }
+  std::vector<std::pair<std::array<cd, 4>, std::array<cd, 4>>> terms;
+  if (g.kind == SF_CZ) {
+    // Eq. 1: CZ = P0 (x) I + P1 (x) Z
+    terms.push_back({{1, 0, 0, 0}, {1, 0, 0, 1}});
+    terms.push_back({{0, 0, 0, 1}, {1, 0, 0, -1}});
+  } else if (decomposition == SF_DEC_BLOCK4) {
+    // Eq. 4way: P0 (x) U00 + P1 (x) U11 + |0><1| (x) U01 + |1><0| (x) U10
+    auto blk = [&](int i, int j) {
+      return std::array<cd, 4>{U[4 * (2 * i) + 2 * j], U[4 * (2 * i) + 2 * j + 1],
+                               U[4 * (2 * i + 1) + 2 * j], U[4 * (2 * i + 1) + 2 * j + 1]};
+    };
+    terms.push_back({{1, 0, 0, 0}, blk(0, 0)});
+    terms.push_back({{0, 0, 0, 1}, blk(1, 1)});
+    terms.push_back({{0, 1, 0, 0}, blk(0, 1)});
+    terms.push_back({{0, 0, 1, 0}, blk(1, 0)});
+  } else {
+    // operator-Schmidt: R[(a a'), (b b')] = U[(a b), (a' b')] = sum_k s_k u_k v_k^H
+    cd R[16], Us[16], V[16];
+    double s[4];
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++)
+        for (int ap = 0; ap < 2; ap++)
+          for (int bp = 0; bp < 2; bp++) R[4 * (2 * a + ap) + (2 * b + bp)] = U[4 * (2 * a + b) + (2 * ap + bp)];
+    svd4(R, Us, s, V);
+    for (int k = 0; k < 4; k++) {
+      if (s[k] < 1e-14) continue;
+      std::array<cd, 4> A, B;
+      for (int i = 0; i < 4; i++) {
+        A[i] = Us[4 * i + k];
+        B[i] = s[k] * std::conj(V[4 * i + k]);
+      }
+      for (int i = 0; i < 4; i++)
+        if (std::abs(A[i]) > 1e-12) {
+          cd ph = A[i] / std::abs(A[i]);
+          for (auto& v : A) v /= ph;
+          for (auto& v : B) v *= ph;
+          break;
+        }
+      terms.push_back({A, B});
+    }
+  }
+  int r = 1;
+  while (r < (int)terms.size()) r *= 2;
+  while ((int)terms.size() < r) terms.push_back({{0, 0, 0, 0}, {0, 0, 0, 0}});
+  x.nterm = r;
+  x.bits = 0;
+  while ((1 << x.bits) < r) x.bits++;
+  for (int d = 0; d < r; d++)
+    for (int i = 0; i < 4; i++) {
+      x.fa[d][i] = terms[d].first[i];
+      x.fb[d][i] = terms[d].second[i];
+    }
+  (void)I;
+}
+
+// Classify a per-digit factor set into a half op (PROJ / XPHASE / XSEL).
+HOp cross_op(int pos, int xi, int nterm, const cd f[4][4]) {
+  HOp o;
+  o.p0 = pos;
+  o.xi = xi;
+  o.nterm = nterm;
+  bool proj = true, phase = true;
+  for (int d = 0; d < nterm; d++) {
+    const cd* m = f[d];
+    bool is_p0 = near(m[0], 1) && near(m[1], 0) && near(m[2], 0) && near(m[3], 0);
+    bool is_p1 = near(m[0], 0) && near(m[1], 0) && near(m[2], 0) && near(m[3], 1);
+    if (is_p0) o.pv[d] = 0;
+    else if (is_p1) o.pv[d] = 1;
+    else proj = false;
+    bool dg = near(m[1], 0) && near(m[2], 0) && near(m[0], 1) && omega_exp(m[3]) >= 0;
+    if (dg) o.tw[d] = omega_exp(m[3]);
+    else phase = false;
+    for (int i = 0; i < 4; i++) o.tm[d][i] = m[i];
+  }
+  o.kind = proj ? H_PROJ : (phase ? H_XPHASE : H_XSEL);
+  return o;
+}
+
+// Half op of a local gate (positions already mapped).
+HOp local_op(const Gate& g, int p0, int p1, cd& global) {
+  HOp o;
+  o.p0 = p0;
+  o.p1 = p1;
+  const cd* m = g.m;
+  if (g.nq() == 2) {
+    if (g.kind == SF_CZ) {
+      o.kind = H_CZ;
+    } else {
+      o.kind = H_G2;
+      for (int i = 0; i < 16; i++) o.m[i] = m[i];
+    }
+    return o;
+  }
+  if (g.kind == SF_H) { o.kind = H_G1; o.fast = DOP_H; o.scale_e = 1; }
+  else if (g.kind == SF_X_HALF) { o.kind = H_G1; o.fast = DOP_XH; o.scale_e = 2; }
+  else if (g.kind == SF_Y_HALF) { o.kind = H_G1; o.fast = DOP_YH; o.scale_e = 2; }
+  for (int i = 0; i < 4; i++) o.m[i] = m[i];
+  if (o.kind == H_G1) return o;
+  bool diag = near(m[1], 0, 0) && near(m[2], 0, 0);
+  if (diag) {
+    // diag(a, b) = a * diag(1, b/a); a power of e^{i pi/4} ratio -> mod-8 phase
+    if (std::abs(m[0]) > 0) {
+      cd ratio = m[3] / m[0];
+      int w = omega_exp(ratio);
+      if (w >= 0 && std::abs(std::abs(m[0]) - 1.0) < 1e-15) {
+        o.kind = H_PHASE1;
+        o.w = w;
+        global *= m[0];
+        return o;
+      }
+    }
+    o.kind = H_DMUL;
+    o.m[0] = m[0];
+    o.m[1] = m[3];
+    return o;
+  }
+  o.kind = H_G1;
+  return o;
+}
+
+uint64_t op_posmask(const HOp& o) {
+  uint64_t b = 1ull << o.p0;
+  if (o.p1 >= 0) b |= 1ull << o.p1;
+  return b;
+}
+
+// ------------------------------------------------------- program emission
+struct Emitter {
+  PassPlan& pp;
+  explicit Emitter(PassPlan& p) : pp(p) {}
+  int add_mats(const cd* m, int count) {  // returns float2 index
+    int at = (int)pp.mats.size() / 2;
+    for (int i = 0; i < count; i++) {
+      pp.mats.push_back((float)m[i].real());
+      pp.mats.push_back((float)m[i].imag());
+    }
+    return at;
+  }
+};
+
+bool emit_stage_ops(const std::vector<const HOp*>& ops, const DevStage& st, const int* local_of,
+                    PassPlan& pp) {
+  Emitter em(pp);
+  auto reg_of = [&](int pos) {
+    int lb = local_of[pos];
+    for (int j = 0; j < st.r; j++)
+      if (st.rbit[j] == lb) return j;
+    return -1;
+  };
+  int cur_group = -1;
+  std::vector<int> wsum(32, 0);
+  auto close_group = [&]() {
+    if (cur_group < 0) return;
+    DevPhaseGroup& g = pp.phases[cur_group];
+    g.m1 = g.m2 = g.m4 = 0;
+    for (int p = 0; p < 32; p++) {
+      int w = ((wsum[p] % 8) + 8) % 8;
+      if (w & 1) g.m1 |= 1u << p;
+      if (w & 2) g.m2 |= 1u << p;
+      if (w & 4) g.m4 |= 1u << p;
+    }
+    std::fill(wsum.begin(), wsum.end(), 0);
+    cur_group = -1;
+  };
+  auto open_group = [&]() {
+    if (cur_group >= 0) return true;
+    if ((int)pp.phases.size() >= MAX_PHASE_GROUPS) return false;
+    DevPhaseGroup g;
+    std::memset(&g, 0, sizeof(g));
+    pp.phases.push_back(g);
+    cur_group = (int)pp.phases.size() - 1;
+    DevOp d{DOP_PHASE, 0, 0, -1, cur_group};
+    pp.ops.push_back(d);
+    return true;
+  };
+  for (const HOp* o : ops) {
+    if (o->kind == H_CZ || o->kind == H_PHASE1 || o->kind == H_XPHASE) {
+      if (!open_group()) return false;
+      DevPhaseGroup& g = pp.phases[cur_group];
+      if (o->kind == H_PHASE1) {
+        wsum[o->p0] += o->w;
+      } else if (o->kind == H_CZ) {
+        // a repeated pair cancels (CZ^2 = I)
+        int a = std::min(o->p0, o->p1), b = std::max(o->p0, o->p1);
+        bool found = false;
+        for (int i = 0; i < g.ncz; i++)
+          if (g.cz[i][0] == a && g.cz[i][1] == b) {
+            g.cz[i][0] = g.cz[g.ncz - 1][0];
+            g.cz[i][1] = g.cz[g.ncz - 1][1];
+            g.ncz--;
+            found = true;
+            break;
+          }
+        if (!found) {
+          if (g.ncz >= MAX_CZ_PER_GROUP) {
+            close_group();
+            if (!open_group()) return false;
+          }
+          DevPhaseGroup& g2 = pp.phases[cur_group];
+          g2.cz[g2.ncz][0] = (int8_t)a;
+          g2.cz[g2.ncz][1] = (int8_t)b;
+          g2.ncz++;
+        }
+      } else {
+        if (g.nsel >= MAX_SEL_PER_GROUP) {
+          close_group();
+          if (!open_group()) return false;
+        }
+        DevPhaseGroup& g2 = pp.phases[cur_group];
+        auto& s = g2.sel[g2.nsel++];
+        s.pos = (int8_t)o->p0;
+        s.xi = (int8_t)o->xi;
+        for (int d = 0; d < 4; d++) s.w[d] = (uint8_t)(d < o->nterm ? o->tw[d] : 0);
+      }
+      continue;
+    }
+    close_group();
+    DevOp d{0, 0, 0, -1, 0};
+    switch (o->kind) {
+      case H_G1:
+        d.a = reg_of(o->p0);
+        if (o->fast) {
+          d.code = o->fast;
+        } else {
+          d.code = DOP_G1;
+          d.arg = em.add_mats(o->m, 4);
+        }
+        break;
+      case H_XSEL: {
+        d.code = DOP_G1SEL;
+        d.a = reg_of(o->p0);
+        d.xi = o->xi;
+        cd buf[16];
+        for (int t = 0; t < 4; t++)
+          for (int i = 0; i < 4; i++) buf[4 * t + i] = t < o->nterm ? o->tm[t][i] : cd(0);
+        d.arg = em.add_mats(buf, 16);
+        break;
+      }
+      case H_G2:
+        d.code = DOP_G2;
+        d.a = reg_of(o->p0);
+        d.b = reg_of(o->p1);
+        d.arg = em.add_mats(o->m, 16);
+        break;
+      case H_DMUL:
+        d.code = DOP_DMUL;
+        d.a = o->p0;
+        d.arg = em.add_mats(o->m, 2);
+        break;
+      default:
+        fail(SF_EINVAL, "internal: unexpected op kind in stage");
+    }
+    if ((d.code == DOP_G1 || d.code == DOP_G1SEL || d.code == DOP_G2 || d.code <= DOP_YH) && d.a < 0)
+      fail(SF_EINVAL, "internal: op bit not in register block");
+    pp.ops.push_back(d);
+  }
+  close_group();
+  return (int)pp.mats.size() <= 2 * MAX_MATS && (int)pp.ops.size() <= MAX_OPS;
+}
+
+DevPin to_dev(const Pin& p) {
+  DevPin d;
+  d.pos = (int8_t)p.pos;
+  d.xi = (int8_t)p.xi;
+  for (int i = 0; i < 4; i++) d.v[i] = (uint8_t)p.v[i];
+  return d;
+}
+
+// Plan one segment of one half into passes. ops are consumed in order.
+void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins, bool gen_input,
+                  int tile_bits, int fuse_bits, SegmentPlan& out) {
+  std::vector<const HOp*> rem;
+  for (auto& o : seg_ops) {
+    if (o.kind == H_PROJ) {
+      Pin p;
+      p.pos = o.p0;
+      p.xi = o.xi;
+      for (int d = 0; d < 4; d++) p.v[d] = o.pv[d];
+      pins.push_back(p);
+    } else {
+      rem.push_back(&o);
+    }
+  }
+  const int k = std::min(tile_bits, m);
+  const int L = std::min(5, k);
+  // register bits: at most the fusion width, at least enough that a tile
+  // needs no more than 512 threads, and leave >= 2^min(5,k-1) threads per tile
+  int R = std::max(1, std::min(fuse_bits, k - std::min(5, k - 1)));
+  R = std::min(MAX_R, std::max(R, k - 9));
+  int res = 0;
+  cd sigma = 1.0;
+  bool first = true;
+  out.passes.clear();
+  out.n_stages = 0;
+  while (first || !rem.empty()) {
+    int cap = MAX_OPS;
+    PassPlan pp;
+    std::vector<const HOp*> taken, deferred;
+    while (true) {
+      pp = PassPlan();
+      taken.clear();
+      deferred.clear();
+      uint64_t S = (L >= 64) ? ~0ull : ((1ull << L) - 1);
+      uint64_t blocked = 0;
+      for (const HOp* o : rem) {
+        uint64_t b = op_posmask(*o);
+        if ((int)taken.size() >= cap || (b & blocked)) {
+          blocked |= b;
+          deferred.push_back(o);
+          continue;
+        }
+        if (o->diag()) {
+          taken.push_back(o);
+          continue;
+        }
+        uint64_t need = b & ~S;
+        if (__builtin_popcountll(S | need) <= k) {
+          S |= need;
+          taken.push_back(o);
+        } else {
+          blocked |= b;
+          deferred.push_back(o);
+        }
+      }
+      // pins removed by this pass: positions with a non-diagonal op
+      uint64_t nd = 0;
+      for (const HOp* o : taken)
+        if (!o->diag()) nd |= op_posmask(*o);
+      uint64_t pinned = 0;
+      for (auto& p : pins) pinned |= 1ull << p.pos;
+      // fill the active set with the lowest unpinned positions
+      for (int p = 0; p < m && __builtin_popcountll(S) < k; p++)
+        if (!((S >> p) & 1) && !((pinned >> p) & 1)) S |= 1ull << p;
+      for (int p = 0; p < m && __builtin_popcountll(S) < k; p++)
+        if (!((S >> p) & 1)) S |= 1ull << p;
+      DevPass& dp = pp.dev;
+      std::memset(&dp, 0, sizeof(dp));
+      dp.m = m;
+      dp.k = k;
+      dp.L = L;
+      dp.R = R;
+      int local_of[64];
+      for (int p = 0; p < 64; p++) local_of[p] = -1;
+      int j = 0;
+      for (int p = 0; p < m; p++)
+        if ((S >> p) & 1) {
+          dp.gpos[j] = (int8_t)p;
+          local_of[p] = j++;
+        }
+      dp.n_free = 0;
+      for (int p = 0; p < m; p++)
+        if (!((S >> p) & 1) && !((pinned >> p) & 1)) dp.freepos[dp.n_free++] = (int8_t)p;
+      if ((int)pins.size() > MAX_PINS) fail(SF_EUNSUPPORTED, "too many pending projections");
+      dp.n_pin_in = (int)pins.size();
+      for (size_t i = 0; i < pins.size(); i++) dp.pin_in[i] = to_dev(pins[i]);
+      std::vector<Pin> pout;
+      for (auto& p : pins)
+        if (!((nd >> p.pos) & 1)) pout.push_back(p);
+      dp.n_pin_out = (int)pout.size();
+      for (size_t i = 0; i < pout.size(); i++) dp.pin_out[i] = to_dev(pout[i]);
+      dp.gen_input = (first && gen_input) ? 1 : 0;
+      // scale bookkeeping (exact powers of two applied in the pass)
+      int e = 0;
+      for (const HOp* o : taken)
+        if (o->kind == H_G1 && o->fast) e += o->scale_e;
+      int t = res + e;
+      int shift = t / 2;
+      dp.post_scale = std::ldexp(1.0f, -shift);
+      // register stages
+      std::vector<const HOp*> srem = taken;
+      bool ok = true;
+      while (!srem.empty()) {
+        uint64_t Sreg = 0, sblocked = 0;
+        std::vector<const HOp*> st_ops, st_def;
+        for (const HOp* o : srem) {
+          uint64_t b = op_posmask(*o);
+          if (b & sblocked) {
+            sblocked |= b;
+            st_def.push_back(o);
+            continue;
+          }
+          if (o->diag()) {
+            st_ops.push_back(o);
+            continue;
+          }
+          uint64_t lb = 1ull << local_of[o->p0];
+          if (o->p1 >= 0) lb |= 1ull << local_of[o->p1];
+          uint64_t need = lb & ~Sreg;
+          if (__builtin_popcountll(Sreg | need) <= R) {
+            Sreg |= need;
+            st_ops.push_back(o);
+          } else {
+            sblocked |= b;
+            st_def.push_back(o);
+          }
+        }
+        for (int lb = k - 1; lb >= 0 && __builtin_popcountll(Sreg) < R; lb--)
+          if (!((Sreg >> lb) & 1)) Sreg |= 1ull << lb;
+        DevStage st;
+        std::memset(&st, 0, sizeof(st));
+        st.r = R;
+        int q = 0;
+        for (int lb = 0; lb < k; lb++)
+          if ((Sreg >> lb) & 1) st.rbit[q++] = (int8_t)lb;
+        st.op_begin = (int)pp.ops.size();
+        if (!emit_stage_ops(st_ops, st, local_of, pp)) {
+          ok = false;
+          break;
+        }
+        st.op_end = (int)pp.ops.size();
+        pp.stages.push_back(st);
+        if ((int)pp.stages.size() > MAX_STAGES) {
+          ok = false;
+          break;
+        }
+        srem = st_def;
+      }
+      if (ok) {
+        res = t - 2 * shift;
+        sigma *= std::pow(2.0, -0.5 * e) / std::ldexp(1.0, -shift);
+        break;
+      }
+      if (cap <= 1) fail(SF_EUNSUPPORTED, "a single gate exceeds the pass program limits");
+      cap = std::max(1, (int)taken.size() / 2);
+    }
+    pp.dev.n_stages = (int)pp.stages.size();
+    out.n_stages += pp.dev.n_stages;
+    out.passes.push_back(std::move(pp));
+    rem = deferred;
+    // pins after this pass
+    uint64_t nd = 0;
+    for (const HOp* o : taken)
+      if (!o->diag()) nd |= op_posmask(*o);
+    std::vector<Pin> np;
+    for (auto& p : pins)
+      if (!((nd >> p.pos) & 1)) np.push_back(p);
+    pins = np;
+    first = false;
+  }
+  // the residual sqrt2 factor stays in sigma; stored values carry it
+  out.pins_out = pins;
+  out.scale = sigma;
+  (void)res;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ plan create
+Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
+  Plan* P = new Plan();
+  try {
+    P->opts = o;
+    P->circ = c;
+    const int n = c.n;
+    uint64_t all = (n == 64) ? ~0ull : ((1ull << n) - 1);
+    uint64_t bm = o.side_b_mask ? o.side_b_mask : auto_cut(c);
+    if (bm & ~all) fail(SF_EINVAL, "side_b_mask has bits beyond the qubit count");
+    if (bm == 0 || bm == all) fail(SF_EINVAL, "both halves must be non-empty");
+    P->side_b_mask = bm;
+    auto inB = [&](int q) { return (bm >> q) & 1; };
+    int mB = __builtin_popcountll(bm), mA = n - mB;
+    if (mA > 32 || mB > 32) fail(SF_EUNSUPPORTED, "a half of more than 32 qubits");
+    if (mA < 1 || mB < 1) fail(SF_EINVAL, "empty half");
+    P->tile_bits = o.tile_bits > 0 ? std::min(o.tile_bits, MAX_K) : 13;
+    P->fuse_bits = o.fuse_bits > 0 ? std::min(o.fuse_bits, MAX_R) : 5;
+    if (P->tile_bits < 6) P->tile_bits = 6;
+
+    // cross gates in time order (cycle, lower qubit, higher qubit)
+    std::vector<int> xg;
+    for (size_t i = 0; i < c.gates.size(); i++) {
+      const Gate& g = c.gates[i];
+      if (g.nq() == 2 && inB(g.q0) != inB(g.q1)) xg.push_back((int)i);
+    }
+    std::stable_sort(xg.begin(), xg.end(), [&](int a, int b) {
+      const Gate &ga = c.gates[a], &gb = c.gates[b];
+      if (ga.cycle != gb.cycle) return ga.cycle < gb.cycle;
+      int la = std::min(ga.q0, ga.q1), lb = std::min(gb.q0, gb.q1);
+      if (la != lb) return la < lb;
+      return std::max(ga.q0, ga.q1) < std::max(gb.q0, gb.q1);
+    });
+    if ((int)xg.size() > MAX_CROSS) fail(SF_EUNSUPPORTED, "more than 64 cross gates");
+    std::map<int, int> xindex;
+    for (size_t i = 0; i < xg.size(); i++) {
+      const Gate& g = c.gates[xg[i]];
+      CrossGate x;
+      x.gate_index = xg[i];
+      x.cycle = g.cycle;
+      bool q0a = !inB(g.q0);
+      x.qa = q0a ? g.q0 : g.q1;
+      x.qb = q0a ? g.q1 : g.q0;
+      decompose(g, q0a, o.decomposition, x);
+      P->cross.push_back(x);
+      xindex[xg[i]] = (int)i;
+    }
+    int total = 0;
+    for (auto& x : P->cross) total += x.bits;
+    if (total > 63) fail(SF_EUNSUPPORTED, "more than 63 path bits");
+    P->path_bits = total;
+    int sh = total;
+    for (auto& x : P->cross) {
+      sh -= x.bits;
+      x.shift = sh;
+    }
+    // levels: cross gates of one cycle
+    for (size_t i = 0; i < P->cross.size(); i++) {
+      if (P->levels.empty() || P->levels.back().cycle != P->cross[i].cycle) {
+        Level L;
+        L.cycle = P->cross[i].cycle;
+        L.first_cross = (int)i;
+        L.n_cross = 0;
+        L.bits = 0;
+        P->levels.push_back(L);
+      }
+      Level& L = P->levels.back();
+      L.n_cross++;
+      L.bits += P->cross[i].bits;
+      L.shift = P->cross[i].shift;
+    }
+    const int nL = (int)P->levels.size();
+    P->xs = o.select_prefix_bits >= 0 ? std::min(o.select_prefix_bits, total) : std::max(0, total - 7);
+
+    // layouts: the last level's cut qubits take the lowest positions
+    for (int side = 0; side < 2; side++) {
+      HalfPlan& H = side ? P->B : P->A;
+      H.m = side ? mB : mA;
+      H.pos_of.assign(n, -1);
+      std::vector<int> order;
+      if (nL > 0) {
+        const Level& L = P->levels.back();
+        for (int i = 0; i < L.n_cross; i++) {
+          const CrossGate& x = P->cross[L.first_cross + i];
+          order.push_back(side ? x.qb : x.qa);
+        }
+      }
+      for (int q = 0; q < n; q++)
+        if ((int)inB(q) == side && std::find(order.begin(), order.end(), q) == order.end())
+          order.push_back(q);
+      H.qubits = order;
+      for (size_t p = 0; p < order.size(); p++) H.pos_of[order[p]] = (int)p;
+      H.seg_ops.assign(nL + 1, {});
+    }
+    // segment of a gate: the number of levels whose cycle <= gate cycle
+    // (local gates of a level's cycle run after its cross gates)
+    std::vector<cd> seg_global(2 * (nL + 1), cd(1.0));
+    for (size_t i = 0; i < c.gates.size(); i++) {
+      const Gate& g = c.gates[i];
+      int s = 0;
+      while (s < nL && P->levels[s].cycle <= g.cycle) s++;
+      auto it = xindex.find((int)i);
+      if (it != xindex.end()) {
+        const CrossGate& x = P->cross[it->second];
+        // s == level index + 1 for a cross gate
+        P->A.seg_ops[s].push_back(cross_op(P->A.pos_of[x.qa], it->second, x.nterm, x.fa));
+        P->B.seg_ops[s].push_back(cross_op(P->B.pos_of[x.qb], it->second, x.nterm, x.fb));
+        continue;
+      }
+      int side = inB(g.q0);
+      HalfPlan& H = side ? P->B : P->A;
+      int p0 = H.pos_of[g.q0], p1 = g.nq() == 2 ? H.pos_of[g.q1] : -1;
+      H.seg_ops[s].push_back(local_op(g, p0, p1, seg_global[2 * s + side]));
+    }
+    // cross ops first within their segment (they commute with the local
+    // gates of the same cycle, which act on other qubits)
+    for (int side = 0; side < 2; side++) {
+      HalfPlan& H = side ? P->B : P->A;
+      for (auto& ops : H.seg_ops)
+        std::stable_partition(ops.begin(), ops.end(), [](const HOp& o) {
+          return o.kind == H_PROJ || o.kind == H_XPHASE || o.kind == H_XSEL ? o.xi >= 0 : false;
+        });
+    }
+    // root: absorb each qubit's leading H into the generated uniform state
+    for (int side = 0; side < 2; side++) {
+      HalfPlan& H = side ? P->B : P->A;
+      H.root_pins.clear();
+      int h = 0;
+      auto& ops0 = H.seg_ops[0];
+      std::vector<bool> erase(ops0.size(), false);
+      for (int p = 0; p < H.m; p++) {
+        bool absorbed = false;
+        for (size_t i = 0; i < ops0.size(); i++) {
+          const HOp& op = ops0[i];
+          if (op.p0 == p || op.p1 == p) {
+            if (op.kind == H_G1 && op.fast == DOP_H) {
+              erase[i] = true;
+              absorbed = true;
+              h++;
+            }
+            break;
+          }
+        }
+        if (!absorbed) {
+          Pin pin;
+          pin.pos = p;
+          pin.xi = -1;
+          pin.v[0] = pin.v[1] = pin.v[2] = pin.v[3] = 0;
+          H.root_pins.push_back(pin);
+        }
+      }
+      std::vector<HOp> kept;
+      for (size_t i = 0; i < ops0.size(); i++)
+        if (!erase[i]) kept.push_back(ops0[i]);
+      ops0 = kept;
+      H.root_scale = std::pow(2.0, -0.5 * h);
+    }
+    // deferral of the last level into the gather
+    P->deferred = false;
+    if (nL > 0 && o.defer_last_level && o.exec_mode != SF_EXEC_PLAIN) {
+      const Level& L = P->levels.back();
+      bool ok = L.n_cross <= MAX_DEFER;
+      int nterm = ok ? P->cross[L.first_cross].nterm : 0;
+      for (int i = 0; ok && i < L.n_cross; i++)
+        if (P->cross[L.first_cross + i].nterm != nterm || nterm > 4) ok = false;
+      std::vector<std::vector<HOp>> kept(2);
+      cd Vm[2][MAX_DEFER][4];
+      for (int side = 0; side < 2 && ok; side++) {
+        HalfPlan& H = side ? P->B : P->A;
+        const auto& ops = H.seg_ops[nL];
+        std::vector<bool> drop(ops.size(), false);
+        for (int i = 0; i < L.n_cross && ok; i++) {
+          const CrossGate& x = P->cross[L.first_cross + i];
+          int pos = H.pos_of[side ? x.qb : x.qa];
+          cd V[4] = {1, 0, 0, 1};
+          int phase = 0;  // 0: before, 1: diagonal run, 2: one-qubit tail
+          bool factor_diag = true;
+          for (int d = 0; d < x.nterm; d++) {
+            const cd* f = side ? x.fb[d] : x.fa[d];
+            if (!near(f[1], 0) || !near(f[2], 0)) factor_diag = false;
+          }
+          for (size_t j = 0; j < ops.size() && ok; j++) {
+            const HOp& op = ops[j];
+            if (op.p0 != pos && op.p1 != pos) continue;
+            if (op.xi == L.first_cross + i && phase == 0) {
+              drop[j] = true;
+              phase = 1;
+              continue;
+            }
+            if (phase == 0) continue;
+            bool one_q = op.p1 < 0;
+            if (phase == 1 && op.diag() && op.kind != H_XPHASE) {
+              if (!factor_diag) ok = false;
+              continue;
+            }
+            if (!one_q || op.xi >= 0) {
+              ok = false;
+              break;
+            }
+            // a one-qubit op joins the deferred tail V
+            cd g[4];
+            if (op.kind == H_G1) {
+              for (int t = 0; t < 4; t++) g[t] = op.m[t];
+            } else if (op.kind == H_PHASE1) {
+              g[0] = 1; g[1] = 0; g[2] = 0; g[3] = omega(op.w);
+            } else if (op.kind == H_DMUL) {
+              g[0] = op.m[0]; g[1] = 0; g[2] = 0; g[3] = op.m[1];
+            } else {
+              ok = false;
+              break;
+            }
+            mul2(g, V, V);
+            drop[j] = true;
+            phase = 2;
+          }
+          if (phase == 0) ok = false;
+          for (int t = 0; t < 4; t++) Vm[side][i][t] = V[t];
+        }
+        if (!ok) break;
+        for (size_t j = 0; j < ops.size(); j++)
+          if (!drop[j]) kept[side].push_back(ops[j]);
+      }
+      if (ok) {
+        P->deferred = true;
+        P->defer_bits = L.bits;
+        std::memset(P->ma, 0, sizeof(P->ma));
+        std::memset(P->mb, 0, sizeof(P->mb));
+        for (int i = 0; i < L.n_cross; i++) {
+          const CrossGate& x = P->cross[L.first_cross + i];
+          for (int d = 0; d < x.nterm; d++) {
+            cd ma[4], mb[4];
+            mul2(Vm[0][i], x.fa[d], ma);
+            mul2(Vm[1][i], x.fb[d], mb);
+            for (int t = 0; t < 4; t++) {
+              P->ma[i][d][2 * t] = (float)ma[t].real();
+              P->ma[i][d][2 * t + 1] = (float)ma[t].imag();
+              P->mb[i][d][2 * t] = (float)mb[t].real();
+              P->mb[i][d][2 * t + 1] = (float)mb[t].imag();
+            }
+          }
+        }
+        P->A.seg_ops.push_back(kept[0]);  // index nL + 1: deferred last segment
+        P->B.seg_ops.push_back(kept[1]);
+      }
+    }
+    // pass programs
+    for (int side = 0; side < 2; side++) {
+      HalfPlan& H = side ? P->B : P->A;
+      H.seg.assign(nL + 1, SegmentPlan());
+      std::vector<Pin> pins = H.root_pins;
+      for (int s = 0; s <= nL; s++) {
+        plan_segment(H.m, H.seg_ops[s], pins, s == 0, P->tile_bits, P->fuse_bits, H.seg[s]);
+        H.seg[s].scale *= seg_global[2 * s + side];
+        pins = H.seg[s].pins_out;
+      }
+      if (P->deferred) {
+        std::vector<Pin> pin_in = nL >= 1 ? H.seg[nL - 1].pins_out : H.root_pins;
+        plan_segment(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, P->tile_bits, P->fuse_bits,
+                     H.last_deferred);
+        H.last_deferred.scale *= seg_global[2 * nL + side];
+      }
+      // gather byte tables: bitstring byte -> layout index bits (deferred
+      // positions excluded; the gather adds them)
+      H.tab.assign(8 * 256, 0);
+      int ndef = P->deferred ? P->levels.back().n_cross : 0;
+      for (int b = 0; b < 8; b++)
+        for (int v = 0; v < 256; v++) {
+          uint32_t r = 0;
+          for (int t = 0; t < 8; t++) {
+            int q = 8 * b + t;
+            if (q >= n || !((v >> t) & 1)) continue;
+            int pos = H.pos_of[q];
+            if (pos < 0 || pos < ndef) continue;
+            r |= 1u << pos;
+          }
+          H.tab[b * 256 + v] = r;
+        }
+    }
+    if (P->A.root_scale == 0.0 || P->B.root_scale == 0.0) fail(SF_EINVAL, "internal scale");
+  } catch (...) {
+    delete P;
+    throw;
+  }
+  return P;
+}
+
+void plan_destroy(Plan* p) {
+  if (!p) return;
+  exec_release_cache(*p);
+  delete p;
+}
+
+// -------------------------------------------------------------- selection
+static uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Keyed 4-round Feistel permutation of [0, 2^w) with cycle walking.
+uint64_t feistel(uint64_t v, int w, uint64_t key) {
+  if (w == 0) return 0;
+  int h = (w + 1) / 2;
+  uint64_t hm = (h >= 64) ? ~0ull : ((1ull << h) - 1);
+  uint64_t lim = (w >= 64) ? ~0ull : (1ull << w);
+  while (true) {
+    uint64_t L = v >> h, R = v & hm;
+    for (int r = 0; r < 4; r++) {
+      uint64_t f = mix64(key ^ (R + (uint64_t)(r + 1) * 0x9E3779B97F4A7C15ull)) & hm;
+      uint64_t nl = R;
+      R = L ^ f;
+      L = nl;
+    }
+    v = (L << h) | R;
+    if (w >= 64 || v < lim) return v;
+  }
+}
+
+std::vector<Range> select_ranges(const Plan& p, const sf_path_sel& s, double* f_actual) {
+  std::vector<Range> out;
+  const int x = p.path_bits;
+  const uint64_t total = 1ull << x;
+  if (s.mode == SF_SEL_RANGE) {
+    if (s.first >= total || s.count > total - s.first) fail(SF_EINVAL, "path range out of bounds");
+    if (s.count) out.push_back({s.first, s.first + s.count});
+    if (f_actual) *f_actual = (double)s.count / (double)total;
+  } else if (s.mode == SF_SEL_FRACTION) {
+    if (!(s.fidelity > 0 && s.fidelity <= 1)) fail(SF_EINVAL, "fidelity must be in (0, 1]");
+    int xs = p.xs;
+    uint64_t np = 1ull << xs;
+    double kf = std::floor(s.fidelity * (double)np + 1e-9);
+    uint64_t K = (uint64_t)std::max(1.0, kf);
+    if (K > np) K = np;
+    std::vector<uint64_t> pre(K);
+    for (uint64_t i = 0; i < K; i++) pre[i] = feistel(i, xs, s.seed);
+    std::sort(pre.begin(), pre.end());
+    int sb = x - xs;
+    for (uint64_t v : pre) {
+      uint64_t lo = v << sb, hi = (v + 1) << sb;
+      if (!out.empty() && out.back().hi == lo) out.back().hi = hi;
+      else out.push_back({lo, hi});
+    }
+    if (f_actual) *f_actual = (double)K / (double)np;
+  } else if (s.mode == SF_SEL_LIST) {
+    if (s.n_list < 0 || (s.n_list > 0 && !s.list)) fail(SF_EINVAL, "bad path list");
+    std::vector<uint64_t> ids(s.list, s.list + s.n_list);
+    std::sort(ids.begin(), ids.end());
+    for (size_t i = 0; i < ids.size(); i++) {
+      if (ids[i] >= total) fail(SF_EINVAL, "path id out of range");
+      if (i && ids[i] == ids[i - 1]) fail(SF_EINVAL, "duplicate path id in list");
+      if (!out.empty() && out.back().hi == ids[i]) out.back().hi++;
+      else out.push_back({ids[i], ids[i] + 1});
+    }
+    if (f_actual) *f_actual = (double)s.n_list / (double)total;
+  } else {
+    fail(SF_EINVAL, "unknown selection mode");
+  }
+  return out;
+}
+
+}  // namespace sf

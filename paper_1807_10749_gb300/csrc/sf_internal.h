@@ -1,0 +1,292 @@
+// Internal structures of the sfsim library: circuit, plan (cut, cross-gate
+// terms, path tree levels, fused pass programs) and the device launch records.
+#pragma once
+
+#include <array>
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sfsim.h"
+
+namespace sf {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+struct Error {
+  int code;
+  std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string& msg);
+
+// ----------------------------------------------------------------- circuit
+struct Gate {
+  int cycle = 0;
+  int kind = 0;
+  int q0 = 0, q1 = -1;
+  cd m[16];  // 2x2 (first 4) or 4x4, row-major; basis 2*bit(q0)+bit(q1)
+  int nq() const { return (kind == SF_CZ || kind == SF_ISWAP || kind == SF_U2) ? 2 : 1; }
+};
+
+struct Circuit {
+  int rows = 0, cols = 0, n = 0;
+  std::vector<Gate> gates;  // stable-sorted by cycle
+};
+
+void gate_matrix(Gate& g);  // fills g.m for named kinds
+Circuit* circuit_from_gates(int rows, int cols, const sf_gate* gates, int64_t n_gates);
+Circuit* circuit_parse(const char* text);
+
+// ------------------------------------------------------------------ linalg
+// One-sided Jacobi SVD of a complex 4x4 matrix: R = U diag(s) V^H, s
+// descending.
+void svd4(const cd R[16], cd U[16], double s[4], cd V[16]);
+
+// ----------------------------------------------------------- device limits
+constexpr int MAX_K = 14;          // tile bits (2^14 complex64 = 128 KiB)
+constexpr int MAX_R = 5;           // register bits per thread
+constexpr int MAX_PINS = 12;
+constexpr int MAX_STAGES = 48;
+constexpr int MAX_OPS = 160;
+constexpr int MAX_PHASE_GROUPS = 40;
+constexpr int MAX_CZ_PER_GROUP = 40;
+constexpr int MAX_SEL_PER_GROUP = 8;
+constexpr int MAX_MATS = 640;      // float2 entries of matrices per pass
+constexpr int MAX_NODES = 128;     // nodes per pass launch
+constexpr int MAX_CROSS = 64;
+constexpr int MAX_DEFER = 4;
+constexpr int GATHER_FINALS = 64;  // finals per gather launch
+
+// Device op codes (applied to a thread's register block; bits are
+// register-local indices a, b in [0, r)).
+enum DevOpCode : int32_t {
+  DOP_H = 1,      // [[1,1],[1,-1]] (scale 1/sqrt2 deferred)
+  DOP_XH = 2,     // [[1+i,1-i],[1-i,1+i]] = 2 X^1/2 (scale 1/2 deferred)
+  DOP_YH = 3,     // [[1+i,-1-i],[1+i,1+i]] = 2 Y^1/2 (scale 1/2 deferred)
+  DOP_G1 = 4,     // general 2x2, mats[arg..arg+4)
+  DOP_G1SEL = 5,  // 2x2 chosen by the digit of cross gate xi: mats[arg + 4*d ..]
+  DOP_G2 = 6,     // general 4x4 on (a = high bit of the basis index, b = low)
+  DOP_PHASE = 7,  // phase group phases[arg] (mod-8 powers of e^{i pi/4})
+  DOP_DMUL = 8,   // diagonal (f0, f1) on global half position a: mats[arg], mats[arg+1]
+  DOP_DMULSEL = 9 // as DMUL, pair chosen by digit of cross gate xi: mats[arg + 2*d ..]
+};
+
+struct DevOp {
+  int32_t code;
+  int32_t a, b;
+  int32_t xi;
+  int32_t arg;
+};
+
+// A group of diagonal gates whose product is exp(i pi/4 * k(idx)) with
+//   k = popc(idx&m1) + 2 popc(idx&m2) + 4 popc(idx&m4)
+//       + 4 sum_pairs bit(p0) bit(p1) + sum_sel w_sel(digit) bit(pos)   (mod 8)
+// idx = the global index inside the half state.
+struct DevPhaseGroup {
+  uint32_t m1, m2, m4;
+  int32_t ncz;
+  int8_t cz[MAX_CZ_PER_GROUP][2];
+  int32_t nsel;
+  struct {
+    int8_t pos, xi;
+    uint8_t w[4];  // weight per digit value
+  } sel[MAX_SEL_PER_GROUP];
+};
+
+struct DevPin {
+  int8_t pos;  // global half position
+  int8_t xi;   // -1: constant v[0]; else value v[digit of cross gate xi]
+  uint8_t v[4];
+};
+
+struct DevStage {
+  int32_t r;
+  int8_t rbit[MAX_R];  // tile-local bit index of register bit j
+  int32_t op_begin, op_end;
+};
+
+struct DevPass {
+  int32_t m, k, L;
+  int32_t R;                 // register bits of every stage (threads = 2^(k-R))
+  int32_t n_free;            // inactive bits free to enumerate tiles
+  int8_t freepos[32];        // their global positions, ascending
+  int8_t gpos[MAX_K];        // tile-local bit j -> global position
+  int32_t n_pin_in;
+  DevPin pin_in[MAX_PINS];   // all pins of the input (zero outside)
+  int32_t n_pin_out;
+  DevPin pin_out[MAX_PINS];  // pins of the output (positions not written)
+  int32_t gen_input;         // input = root state: 1 on live entries
+  float post_scale;          // exact power of two applied at store
+  int32_t n_stages;
+};
+
+struct PassNode {
+  const void* in;  // float2*, ignored when gen_input
+  void* out;
+  uint64_t path;   // path id bits that select digits
+};
+
+struct PassLaunch {
+  DevPass pass;
+  DevStage stages[MAX_STAGES];
+  DevOp ops[MAX_OPS];
+  DevPhaseGroup phases[MAX_PHASE_GROUPS];
+  float mats[2 * MAX_MATS];
+  uint8_t xshift[MAX_CROSS];
+  uint8_t xbits[MAX_CROSS];
+  int32_t n_nodes;
+  PassNode nodes[MAX_NODES];
+};
+
+// Gather: per bitstring, sum over the launch's finals of the (deferred)
+// contraction, added to acc in FP64.
+struct GatherFinal {
+  const void* wa;  // float2*
+  const void* wb;
+  uint64_t path;   // digits for pins and leaf lists (group id << defer bits)
+  double sre, sim; // complex scale of this final (sigma_A * sigma_B)
+  int32_t all_leaves;         // 1: every leaf of the deferred level
+  uint64_t leafmask[4];       // else: selected leaf digits (bit b = leaf b)
+};
+
+struct GatherSide {
+  int32_t npin;
+  DevPin pin[MAX_PINS];
+  int8_t dpos[MAX_DEFER];  // layout positions of the deferred qubits
+  int8_t dq[MAX_DEFER];    // their global qubit numbers (bits of x)
+};
+
+struct GatherLaunch {
+  const uint32_t* tabA;  // 8 x 256 byte tables: x byte -> layout index part
+  const uint32_t* tabB;
+  const uint64_t* bits;
+  double* acc;           // 2n doubles
+  int64_t n;
+  int32_t accumulate;    // 0: acc = sum, 1: acc += sum
+  int32_t g;             // deferred gates
+  int32_t nterm_bits;    // log2 terms per deferred gate (1 or 2)
+  GatherSide A, B;
+  float ma[MAX_DEFER][4][8];  // M^A_{i,d} = V^A_i F^A_{i,d}, 2x2 interleaved
+  float mb[MAX_DEFER][4][8];
+  uint8_t xshift[MAX_CROSS];
+  uint8_t xbits[MAX_CROSS];
+  int32_t n_finals;
+  GatherFinal finals[GATHER_FINALS];
+};
+
+// -------------------------------------------------------------- host plan
+struct Pin {
+  int pos;  // half layout position
+  int xi;   // -1 const
+  int v[4];
+};
+
+// Host-side op of a half (positions are layout positions).
+enum HopKind { H_G1, H_G2, H_CZ, H_PHASE1, H_DMUL, H_XSEL, H_XPHASE, H_PROJ };
+struct HOp {
+  int kind;
+  int p0 = -1, p1 = -1;
+  int fast = 0;       // DOP_H / DOP_XH / DOP_YH for H_G1 with that matrix
+  int scale_e = 0;    // deferred factor (1/sqrt2)^scale_e of the fast form
+  int w = 0;          // H_PHASE1: weight (mod 8) of e^{i pi/4}
+  cd m[16];           // matrix (G1: 4, G2: 16, DMUL: 2 diag)
+  int xi = -1;        // cross gate index for X* ops
+  int nterm = 0;
+  cd tm[4][4];        // per-digit 2x2 factor (XSEL), or diag (XPHASE uses tw)
+  int tw[4] = {0, 0, 0, 0};  // XPHASE weights per digit
+  int pv[4] = {0, 0, 0, 0};  // PROJ kept value per digit
+  bool diag() const { return kind == H_CZ || kind == H_PHASE1 || kind == H_DMUL || kind == H_XPHASE; }
+};
+
+struct PassPlan {
+  DevPass dev;
+  std::vector<DevStage> stages;
+  std::vector<DevOp> ops;
+  std::vector<DevPhaseGroup> phases;
+  std::vector<float> mats;
+};
+
+struct SegmentPlan {
+  std::vector<PassPlan> passes;
+  std::vector<Pin> pins_out;  // pins of the segment's output
+  cd scale = 1.0;             // sigma: true = scale * stored (relative to input)
+  int n_stages = 0;
+};
+
+struct HalfPlan {
+  int m = 0;
+  std::vector<int> qubits;    // global qubit at layout position p
+  std::vector<int> pos_of;    // global qubit -> layout position (-1 if not here)
+  std::vector<std::vector<HOp>> seg_ops;  // per segment
+  std::vector<Pin> root_pins; // root input pins (qubits without leading H)
+  cd root_scale = 1.0;
+  std::vector<SegmentPlan> seg;          // per segment, full program
+  SegmentPlan last_deferred;             // last segment without deferred ops
+  std::vector<uint32_t> tab;             // 8 x 256 gather byte tables
+};
+
+struct CrossGate {
+  int gate_index;
+  int cycle;
+  int qa, qb;     // global qubits on side A / B
+  int nterm;      // power of two
+  int bits;
+  int shift;      // path-id bit offset of its digit
+  cd fa[4][4], fb[4][4];  // per-term 2x2 factors
+};
+
+struct Level {
+  int cycle;
+  int first_cross, n_cross;
+  int bits;   // total bits of the level
+  int shift;  // lowest path bit of the level
+};
+
+struct Plan {
+  sf_plan_opts opts;
+  Circuit circ;
+  uint64_t side_b_mask = 0;
+  std::vector<CrossGate> cross;
+  std::vector<Level> levels;
+  int path_bits = 0;
+  int xs = 0;  // FRACTION prefix bits
+  HalfPlan A, B;
+  bool deferred = false;       // last level folded into the gather
+  int defer_bits = 0;          // bits of the last level when deferred
+  float ma[MAX_DEFER][4][8];
+  float mb[MAX_DEFER][4][8];
+  int tile_bits = 13, fuse_bits = 5;
+  // device copies
+  uint32_t* d_tabA = nullptr;
+  uint32_t* d_tabB = nullptr;
+  int device = 0;
+  // executor cache (resident nodes between calls that reuse a workspace)
+  void* cache = nullptr;
+};
+
+Plan* plan_create(const Circuit& c, const sf_plan_opts& o);
+void plan_destroy(Plan* p);
+
+// ------------------------------------------------------------- selection
+struct Range {
+  uint64_t lo, hi;  // [lo, hi)
+};
+// Sorted, disjoint ranges of selected path ids.
+std::vector<Range> select_ranges(const Plan& p, const sf_path_sel& s, double* f_actual);
+uint64_t feistel(uint64_t v, int w, uint64_t key);
+
+// -------------------------------------------------------------- executor
+size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s);
+void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, double* d_out,
+              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache);
+void exec_release_cache(Plan& p);
+
+// ---------------------------------------------------------------- kernels
+void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, void* stream);
+void launch_gather(const GatherLaunch& L, void* stream);
+void launch_zero(double* p, int64_t n_doubles, void* stream);
+
+}  // namespace sf

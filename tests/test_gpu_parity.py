@@ -1,0 +1,232 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (the contract for complex64 halves with FP64 path accumulation):
+max |amp_gpu - amp_oracle| <= 1e-5 * 2^{-n/2}; sums over few paths are also
+held to 3e-5 of the RMS oracle amplitude, since their values are far below
+2^{-n/2}.
+"""
+import numpy as np
+import pytest
+
+from oracle import circuit as ocirc
+from oracle import paths as opaths
+from oracle import sim
+from paper_1807_10749_gb300 import inputs, sfsim
+
+pytestmark = pytest.mark.gpu
+
+ABS_TOL = 1e-5
+REL_TOL = 3e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1807_10749_gb300 import build
+    build.build()
+    sim.build()
+
+
+def check_close(gpu, ref, n, label=""):
+    err = np.abs(gpu - ref)
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    bound = ABS_TOL * 2.0 ** (-n / 2)
+    print(f"{label}: max|d| = {err.max():.3e} (= {err.max() / 2.0 ** (-n / 2):.2e} * 2^-n/2), "
+          f"rms|ref| = {rms:.3e}, rms|d| = {np.sqrt(np.mean(err ** 2)):.3e}")
+    assert err.max() <= bound, f"{label}: {err.max()} > {bound}"
+    assert err.max() <= REL_TOL * rms + 1e-300, f"{label}: {err.max()} > {REL_TOL} * rms {rms}"
+
+
+def workload(name, **kw):
+    w = inputs.WORKLOADS[name]
+    spec = inputs.google_circuit(w["rows"], w["cols"], w["depth"], 1, **kw)
+    return w, spec.text()
+
+
+# ----------------------------------------------------------------- 4x4 (C1)
+def test_4x4_all_paths_equal_state_vector():
+    w, text = workload("4x4_d10")
+    c = ocirc.parse(text)
+    xs = np.arange(1 << 16, dtype=np.uint64)
+    ref = sim.sv_amplitudes(c, xs)
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    amp, fa = p.amplitudes(xs, sfsim.selection("fraction", fidelity=1.0))
+    assert fa == 1.0
+    check_close(amp, ref, 16, "4x4 f=1 all bitstrings")
+    bits = inputs.random_bitstrings(16, 1024, w["bitstring_seed"])
+    amp2, _ = p.amplitudes(bits, sfsim.selection("range", first=0, count=16))
+    check_close(amp2, sim.sv_amplitudes(c, bits), 16, "4x4 1024 random")
+    p.close()
+
+
+def test_4x4_each_path_alone_matches_oracle():
+    """Per-path parity: path numbering and enumeration agree exactly."""
+    w, text = workload("4x4_d10")
+    c = ocirc.parse(text)
+    setup = sim.SFSetup(c, w["side_b_mask"])
+    bits = inputs.random_bitstrings(16, 1024, w["bitstring_seed"])
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    for j in range(16):
+        ref = sim.sf_amplitudes(setup, np.array([j], dtype=np.uint64), bits)
+        amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=[j]))
+        check_close(amp, ref, 16, f"4x4 path {j}")
+    p.close()
+
+
+@pytest.mark.parametrize("kind,dec", [("haar", sfsim.SF_DEC_SCHMIDT), ("haar", sfsim.SF_DEC_BLOCK4),
+                                      ("iswap", sfsim.SF_DEC_BLOCK4)])
+def test_4x4_four_way_branching(kind, dec):
+    """Section 7: non-CZ cross gates branch four ways (Schmidt / Eq. 4way)."""
+    w, text = workload("4x4_d10", haar=(kind == "haar"), iswap=(kind == "iswap"))
+    c = ocirc.parse(text)
+    xs = np.arange(1 << 16, dtype=np.uint64)
+    ref = sim.sv_amplitudes(c, xs)
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"], decomposition=dec)
+    amp, _ = p.amplitudes(xs, sfsim.selection("fraction", fidelity=1.0))
+    check_close(amp, ref, 16, f"4x4 {kind} dec={dec}")
+    # per-path parity for a few paths (tie-free decompositions)
+    if kind == "haar":
+        setup = sim.SFSetup(c, w["side_b_mask"], "block4" if dec == sfsim.SF_DEC_BLOCK4 else "schmidt")
+        bits = inputs.random_bitstrings(16, 512, 5)
+        for j in (0, 37, 255):
+            r = sim.sf_amplitudes(setup, np.array([j], dtype=np.uint64), bits)
+            a, _ = p.amplitudes(bits, sfsim.selection("list", ids=[j]))
+            check_close(a, r, 16, f"4x4 {kind} path {j}")
+    p.close()
+
+
+def test_4x4_plain_equals_batched():
+    w, text = workload("4x4_d10")
+    bits = inputs.random_bitstrings(16, 1024, w["bitstring_seed"])
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    q = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN)
+    sel = sfsim.selection("fraction", fidelity=1.0)
+    a, _ = p.amplitudes(bits, sel)
+    b, _ = q.amplitudes(bits, sel)
+    assert np.abs(a - b).max() <= 1e-6 * 2.0 ** -8
+    p.close()
+    q.close()
+
+
+def test_edge_cases():
+    w, text = workload("4x4_d10")
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    c = ocirc.parse(text)
+    # empty bitstring list, empty selection
+    a, _ = p.amplitudes(np.zeros(0, dtype=np.uint64), sfsim.selection("range", count=16))
+    assert a.size == 0
+    bits = inputs.random_bitstrings(16, 300, 9)
+    a, fa = p.amplitudes(bits, sfsim.selection("range", first=3, count=0))
+    assert fa == 0 and np.all(a == 0)
+    # duplicates and a ragged count
+    bits = np.concatenate([bits[:257], bits[:5]])
+    a, _ = p.amplitudes(bits, sfsim.selection("range", count=16))
+    assert np.array_equal(a[257:], a[:5])
+    check_close(a, sim.sv_amplitudes(c, bits), 16, "ragged 262")
+    # single bitstring, top bits above n ignored? no: bit q >= n is outside
+    a1, _ = p.amplitudes(bits[:1], sfsim.selection("range", count=16))
+    assert a1[0] == a[0]
+    p.close()
+
+
+def test_device_form_matches_host_form():
+    import torch
+    w, text = workload("4x4_d10")
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    bits = inputs.random_bitstrings(16, 1000, 4)
+    sel = sfsim.selection("fraction", fidelity=1.0)
+    host, _ = p.amplitudes(bits, sel)
+    d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
+    d_out = torch.zeros((len(bits), 2), dtype=torch.float64, device="cuda")
+    ws = torch.empty(sfsim.sf_workspace_size(p.handle, len(bits), sel), dtype=torch.uint8, device="cuda")
+    sfsim.sf_amplitudes_device(p.handle, d_bits, sel, d_out, ws)
+    sfsim.sf_amplitudes_device(p.handle, d_bits, sel, d_out, ws, accumulate=True)
+    torch.cuda.synchronize()
+    o = d_out.cpu().numpy()
+    dev = o[:, 0] + 1j * o[:, 1]
+    assert np.abs(dev - 2 * host).max() <= 1e-12 * 2.0 ** -8
+    p.close()
+
+
+# ---------------------------------------------------------------- 5x6 (C2)
+def test_5x6_path_subsets_match_oracle():
+    w, text = workload("5x6_d24")
+    c = ocirc.parse(text)
+    setup = sim.SFSetup(c, w["side_b_mask"])
+    bits = inputs.random_bitstrings(30, 20000, w["bitstring_seed"])
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    for sel, ids in [(sfsim.selection("range", first=5000, count=700), opaths.select_range(5000, 700)),
+                     (sfsim.selection("fraction", fidelity=1 / 32, seed=7),
+                      opaths.select_fraction(setup.x_bits, 1 / 32, 7)[0])]:
+        ref = sim.sf_amplitudes(setup, ids, bits)
+        amp, _ = p.amplitudes(bits, sel)
+        check_close(amp, ref, 30, f"5x6 {len(ids)} paths")
+    p.close()
+
+
+def test_5x6_full_sum_porter_thomas():
+    """All 2^15 paths, 100k bitstrings: E[N p] ~ 1, E[(N p)^2] ~ 2 (Section 4)."""
+    w, text = workload("5x6_d24")
+    bits = inputs.random_bitstrings(30, w["n_bitstrings"], w["bitstring_seed"])
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    amp, _ = p.amplitudes(bits, sfsim.selection("fraction", fidelity=1.0))
+    t = (2.0 ** 30) * np.abs(amp) ** 2
+    print("5x6 PT moments", t.mean(), (t ** 2).mean())
+    assert abs(t.mean() - 1) < 0.03
+    assert abs((t ** 2).mean() - 2) < 0.12
+    p.close()
+
+
+# ---------------------------------------------------------------- 6x7 (C3)
+@pytest.mark.parametrize("kind", ["cz", "haar"])
+def test_6x7_path_list_matches_oracle(kind):
+    w, text = workload("6x7_d26", haar=(kind == "haar"))
+    c = ocirc.parse(text)
+    setup = sim.SFSetup(c, w["side_b_mask"])
+    bits = inputs.random_bitstrings(42, 4096, w["bitstring_seed"])
+    ids = inputs.random_path_list(setup.x_bits, 12 if kind == "cz" else 6, 11)
+    # include a whole last-level group so the deferred contraction is used
+    grp = (int(ids[0]) >> 4) << 4 if kind == "cz" else (int(ids[0]) >> 8) << 8
+    full = np.arange(grp, grp + (16 if kind == "cz" else 256), dtype=np.uint64)
+    ids = np.unique(np.concatenate([ids, full]))
+    if kind == "haar":
+        ids = np.unique(np.concatenate([ids[:6], full[:40]]))
+    ref = sim.sf_amplitudes(setup, ids, bits)
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
+    check_close(amp, ref, 42, f"6x7 {kind} {len(ids)} paths")
+    p.close()
+
+
+# ---------------------------------------------------------------- 7x8 (C4)
+def test_7x8_path_list_matches_oracle():
+    """Full size (28+28 qubits, 2 GiB halves): a seeded path list x 1024
+    bitstrings against the oracle."""
+    w, text = workload("7x8_d40")
+    c = ocirc.parse(text)
+    setup = sim.SFSetup(c, w["side_b_mask"])
+    bits = inputs.random_bitstrings(56, 1024, w["bitstring_seed"])
+    ids = inputs.random_path_list(setup.x_bits, 2, 8)
+    ref = sim.sf_amplitudes(setup, ids, bits)
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
+    check_close(amp, ref, 56, "7x8 2 paths")
+    p.close()
+
+
+def test_7x8_prefix_batched_equals_plain():
+    """One 128-path prefix of the f = 0.5% selection: the batched executor
+    (path tree + last level folded into the gather) equals the plain
+    one-path-at-a-time executor."""
+    w, text = workload("7x8_d40")
+    bits = inputs.random_bitstrings(56, 100000, w["bitstring_seed"])
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    q = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN)
+    ids = sfsim.sf_selection_ids(p.handle, sfsim.selection("fraction", fidelity=0.005, seed=7), cap=128)
+    sel = sfsim.selection("range", first=int(ids[0]), count=128)
+    a, _ = p.amplitudes(bits, sel)
+    b, _ = q.amplitudes(bits, sel)
+    check_close(a, b, 56, "7x8 prefix batched vs plain")
+    p.close()
+    q.close()

@@ -1,0 +1,123 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point include/sfsim.h declares, validates input, plans the
+workloads, and enumerates path selections bit-exactly like the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import circuit as ocirc
+from oracle import paths as opaths
+from oracle import sim
+from paper_1807_10749_gb300 import inputs, sfsim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1807_10749_gb300 import build
+    build.build()
+
+
+def test_library_exports_every_declared_symbol():
+    with open(os.path.join(ROOT, "include", "sfsim.h")) as fh:
+        declared = set(re.findall(r"SF_API\s+[\w\s\*]*?\b(sf_\w+)\s*\(", fh.read()))
+    assert declared == set(sfsim.EXPORTED)
+    lib = sfsim.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_parse_errors_are_reported():
+    for bad in ["0 h 0\n", "grid 2 2\n0 h 9\n", "grid 2 2\n0 cz 0 0\n", "grid 2 2\n1 h 0\n1 t 0\n",
+                "grid 2 2\n0 foo 1\n", "grid 2 2\n0 u1 0 1 2\n"]:
+        with pytest.raises(sfsim.SFError) as e:
+            sfsim.sf_circuit_parse(bad)
+        assert e.value.code == sfsim.SF_EINVAL
+        assert sfsim.sf_last_error()
+
+
+def test_circuit_create_matches_parse():
+    g = sfsim.sf_gate()
+    g.cycle, g.kind, g.q0, g.q1 = 0, sfsim.SF_H, 1, -1
+    c = sfsim.sf_circuit_create(2, 2, [g])
+    assert sfsim.sf_circuit_info(c) == (2, 2, 1)
+    sfsim.sf_circuit_destroy(c)
+    with pytest.raises(sfsim.SFError):
+        g.q0 = 7
+        sfsim.sf_circuit_create(2, 2, [g])
+
+
+@pytest.mark.parametrize("name", list(inputs.WORKLOADS))
+def test_plan_matches_oracle_split(name):
+    """Cut, cross-gate count and path bits agree with the oracle's split."""
+    w = inputs.WORKLOADS[name]
+    spec = inputs.google_circuit(w["rows"], w["cols"], w["depth"], 1)
+    p = sfsim.Plan(spec.text(), side_b_mask=w["side_b_mask"])
+    setup = sim.SFSetup(ocirc.parse(spec.text()), w["side_b_mask"])
+    assert p.info["n_cross"] == setup.n_cross
+    assert p.info["path_bits"] == setup.x_bits
+    assert p.info["m_a"] == len(setup.posA) and p.info["m_b"] == len(setup.posB)
+    st = sfsim.sf_plan_stats(p.handle)
+    assert st["passes_a"] > 0 and st["passes_b"] > 0
+    p.close()
+
+
+def test_auto_cut_is_the_minimal_straight_cut():
+    """Section 8: minimise the larger block, then the number of cross gates.
+    7x8: the vertical cut between columns 3 and 4 gives 28+28 (35 xCZ)."""
+    spec = inputs.google_circuit(7, 8, 40, 1)
+    p = sfsim.Plan(spec.text())
+    assert p.info["m_a"] == 28 and p.info["m_b"] == 28 and p.info["n_cross"] == 35
+    p.close()
+
+
+def test_haar_variant_branches_four_ways():
+    spec = inputs.google_circuit(4, 4, 10, 1, haar=True)
+    w = inputs.WORKLOADS["4x4_d10"]
+    for dec in (sfsim.SF_DEC_SCHMIDT, sfsim.SF_DEC_BLOCK4):
+        p = sfsim.Plan(spec.text(), side_b_mask=w["side_b_mask"], decomposition=dec)
+        assert p.info["path_bits"] == 8
+        p.close()
+
+
+def test_selection_ids_match_oracle_bit_exactly():
+    spec = inputs.google_circuit(5, 6, 24, 1)
+    w = inputs.WORKLOADS["5x6_d24"]
+    p = sfsim.Plan(spec.text(), side_b_mask=w["side_b_mask"])
+    x = p.info["path_bits"]
+    for f in (1.0, 0.25, 1 / 64, 0.001):
+        sel = sfsim.selection("fraction", fidelity=f, seed=7)
+        ids = sfsim.sf_selection_ids(p.handle, sel)
+        want, fa = opaths.select_fraction(x, f, 7)
+        assert np.array_equal(ids, np.sort(want))
+        assert sfsim.sf_selection_size(p.handle, sel) == (len(want), fa)
+    sel = sfsim.selection("range", first=100, count=37)
+    assert np.array_equal(sfsim.sf_selection_ids(p.handle, sel), opaths.select_range(100, 37))
+    lst = inputs.random_path_list(x, 50, 3)
+    sel = sfsim.selection("list", ids=lst[::-1])
+    assert np.array_equal(sfsim.sf_selection_ids(p.handle, sel), np.sort(lst))
+    # errors: out of range, duplicates, bad fidelity
+    for bad in (sfsim.selection("range", first=1 << x, count=1),
+                sfsim.selection("list", ids=[1, 1]),
+                sfsim.selection("fraction", fidelity=0.0)):
+        with pytest.raises(sfsim.SFError) as e:
+            sfsim.sf_selection_size(p.handle, bad)
+        assert e.value.code == sfsim.SF_EINVAL
+    p.close()
+
+
+def test_feistel_matches_oracle_at_28_bits():
+    """The 7x8 FRACTION selection (x_s = 28) enumerates the oracle's prefixes."""
+    spec = inputs.google_circuit(7, 8, 40, 1)
+    p = sfsim.Plan(spec.text(), side_b_mask=inputs.WORKLOADS["7x8_d40"]["side_b_mask"])
+    sel = sfsim.selection("fraction", fidelity=0.005, seed=7)
+    n, fa = sfsim.sf_selection_size(p.handle, sel)
+    assert n == 1342177 * 128 and fa == 1342177 / 2 ** 28
+    ids = sfsim.sf_selection_ids(p.handle, sel, cap=128 * 64)
+    pre = sorted(opaths.feistel(i, 28, 7) for i in range(1342177))[:64]
+    want = np.array([(q << 7) | s for q in pre for s in range(128)], dtype=np.uint64)
+    assert np.array_equal(ids, want)
+    p.close()
