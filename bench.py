@@ -1,0 +1,327 @@
+"""Benchmark: simulated paths/s of the Schroedinger-Feynman path sum on the
+7x8 grid, depth 1+40+1 (28+28-qubit halves, 35 cut CZs), fidelity f = 0.5%
+(FRACTION selection, seed 7), 1M random 56-bit bitstrings.
+
+A step is one 128-path prefix subtree of the selection (the unit a single
+process of the paper ran, 28 prefix bits + 7 suffix bits), taken in the
+selection's sorted order, through the C ABI with every input resident in HBM.
+`e2e` repeats the measurement through the host-buffer call (bitstrings copied
+in, amplitudes copied out inside the timed region).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank takes every N-th prefix (weak scaling, no collective
+in the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "7x8_d40"
+FIDELITY = 0.005
+SEED = 7
+METRIC = "simulated paths/s at 7x8 depth 1+40+1"
+UNIT = "paths/s"
+
+
+def config_dict(n_bits, extra=None):
+    d = {"workload": "7x8 grid, depth 1+40+1 (v2 one-qubit rule), cut cols 0-3 | 4-7 (28+28 qubits), 35 cut CZs, "
+                     "f = 0.5% (FRACTION, 28 prefix bits, seed 7), 1M random bitstrings; "
+                     "step = one 128-path prefix subtree",
+         "grid": "7x8", "depth": "1+40+1", "fidelity": FIDELITY, "bitstrings": n_bits,
+         "paths_per_step": 128,
+         "l2": "no flush: every pass streams 2 GiB half-states, far larger than the 129 MB L2"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxes.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": float(np.median(sms)), "sm_max_mhz": max(maxes), "samples": len(sms),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1807_10749_gb300", "csrc", "kernels.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n_nodes_bytes_per_launch):
+    """DRAM bytes per pass launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_7x8_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("kernels_cu_sha256_16") != kernel_source_hash():
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_baseline_sample(text, mask, bits_all):
+    """The FP64 oracle as it stands: one selected path of the same workload,
+    both 28-qubit halves evolved from scratch, 1024 of the bitstrings."""
+    from oracle import circuit as ocirc
+    from oracle import sim
+    sim.build()
+    setup = sim.SFSetup(ocirc.parse(text), mask)
+    from oracle import paths as opaths
+    pre, _, _ = opaths.fraction_prefixes(setup.x_bits, FIDELITY, SEED)
+    ids = np.array([pre[0] << (setup.x_bits - 28)], dtype=np.uint64)
+    t0 = time.perf_counter()
+    sim.sf_amplitudes(setup, ids, bits_all[:1024])
+    dt = time.perf_counter() - t0
+    return {"value": len(ids) / dt, "unit": UNIT, "cores": sim.threads(), "kind": "oracle",
+            "sample": f"1 path (prefix {pre[0]}, suffix 0) x 1024 bitstrings of the 7x8 workload, "
+                      f"both halves evolved in FP64 from |0>; {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1807_10749_gb300 import inputs
+    w = inputs.WORKLOADS[WORKLOAD]
+    text = inputs.workload_circuit(WORKLOAD).text()
+    bits = inputs.random_bitstrings(56, 1024, w["bitstring_seed"])
+    from oracle import circuit as ocirc
+    from oracle import paths as opaths
+    from oracle import sim
+    sim.build()
+    setup = sim.SFSetup(ocirc.parse(text), w["side_b_mask"])
+    pre, _, _ = opaths.fraction_prefixes(setup.x_bits, FIDELITY, SEED)
+    times = []
+    for step in range(args.warmup + args.steps):
+        ids = np.array([pre[step % len(pre)] << (setup.x_bits - 28)], dtype=np.uint64)
+        t0 = time.perf_counter()
+        sim.sf_amplitudes(setup, ids, bits)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = len(times) / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": config_dict(1024, {"reference": "FP64 CPU oracle (oracle/core.c, OpenMP)",
+                                         "step": "one path of the selection x 1024 bitstrings"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": sim.threads(), "kind": "oracle",
+                             "sample": "per step one selected path x 1024 bitstrings, FP64 from |0>"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=12)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--bitstrings", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--exec-mode", default="batched", choices=["batched", "plain"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_1807_10749_gb300 import build as sfbuild
+    if rank == 0 or world == 1:
+        sfbuild.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1807_10749_gb300 import inputs, sfsim
+
+    w = inputs.WORKLOADS[WORKLOAD]
+    text = inputs.workload_circuit(WORKLOAD).text()
+    bits = inputs.random_bitstrings(56, args.bitstrings, w["bitstring_seed"])
+    mode = sfsim.SF_EXEC_PLAIN if args.exec_mode == "plain" else sfsim.SF_EXEC_BATCHED
+    plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode)
+    fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
+    n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
+    n_steps_total = args.warmup + args.steps
+    # this rank's prefixes: every world-th 128-path subtree of the sorted selection
+    first_ids = sfsim.sf_selection_ids(plan.handle, fsel, cap=128 * world * (n_steps_total + 2))
+    prefixes = [int(first_ids[128 * (world * s + rank)]) for s in range(n_steps_total + 1)]
+    sels = [sfsim.selection("range", first=p, count=128) for p in prefixes]
+
+    d_bits = torch.from_numpy(bits.view(np.int64)).to(f"cuda:{dev}")
+    d_out = torch.zeros((len(bits), 2), dtype=torch.float64, device=f"cuda:{dev}")
+    ws_bytes = max(sfsim.sf_workspace_size(plan.handle, len(bits), s) for s in sels[:2])
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=f"cuda:{dev}")
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        sfsim.sf_amplitudes_device(plan.handle, d_bits, sels[i], d_out, ws, stream=stream, accumulate=True)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sfsim.sf_plan_profile(plan.handle, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.warmup, n_steps_total):
+        step(i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    pass_n, pass_s, pass_b = sfsim.sf_plan_profile_read(plan.handle, 0)
+    gat_n, gat_s, gat_b = sfsim.sf_plan_profile_read(plan.handle, 1)
+    oth_n, _, _ = sfsim.sf_plan_profile_read(plan.handle, 2)
+    sfsim.sf_plan_profile(plan.handle, False)
+    t_max = elapsed
+    if world > 1:
+        t = torch.tensor([elapsed], device=f"cuda:{dev}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    paths_total = 128 * args.steps * world
+    value = paths_total / t_max
+
+    # end to end through the host-buffer call (H2D bitstrings, D2H amplitudes)
+    host_out = None
+    e2e_steps = max(2, min(args.steps, 6))
+    for i in range(1):
+        plan.amplitudes(bits, sels[i])  # warm the host-form workspace
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t1 = time.perf_counter()
+    for i in range(e2e_steps):
+        host_out, _ = plan.amplitudes(bits, sels[(args.warmup + i) % len(sels)])
+    e2e_wall = time.perf_counter() - t1
+    if world > 1:
+        t = torch.tensor([e2e_wall], device=f"cuda:{dev}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_wall = float(t.item())
+    e2e_value = 128 * e2e_steps * world / e2e_wall
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        achieved = (pass_b / pass_s) / 1e9 if pass_s > 0 else None
+        traffic = ncu_traffic(pass_b / max(1, pass_n))
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline_sample(text, w["side_b_mask"], bits)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
+                                              "paths_selected": n_sel, "parallelism": f"paths x{world}",
+                                              "wall_s": wall}),
+            "roofline": {"kernel": "pass_kernel (fused tile pass)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": pass_b / max(1, pass_n),
+                         "avg_launch_ms": 1e3 * pass_s / max(1, pass_n),
+                         "share_of_step": pass_s / t_max if t_max > 0 else None},
+            "kernels": {"pass": {"launches": pass_n, "seconds": pass_s, "bytes": pass_b},
+                        "gather": {"launches": gat_n, "seconds": gat_s, "bytes": gat_b},
+                        "other": {"launches": oth_n}},
+            "gpu_launches": pass_n + gat_n + oth_n,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(bits),
+                    "d2h_bytes_per_step": 16 * len(bits), "steps": e2e_steps},
+            "clocks": clocks,
+            "cpu_baseline": ({k: v for k, v in cpu.items() if k != "seconds"} if cpu else None),
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -189,6 +189,16 @@ SF_API int sf_server_cancel(sf_server* s, uint64_t ticket);
 SF_API int sf_server_times(sf_server* s, uint64_t ticket, double* queued_s, double* total_s);
 SF_API void sf_server_destroy(sf_server* s);
 
+/* Kernel counters of one plan, for roofline reports. sf_plan_profile resets
+ * them and turns per-launch CUDA-event timing on (enable_timing = 1) or off.
+ * sf_plan_profile_read returns, for kernel 0 (fused tile pass), 1 (gather)
+ * or 2 (other), the launches since the reset, their summed device time in
+ * seconds (0 unless timing was on; blocks until those launches finished)
+ * and their algorithmic bytes (state amplitudes read + written, 8 bytes each,
+ * for passes; bitstrings, gathered amplitudes and accumulators for gathers). */
+SF_API int sf_plan_profile(sf_plan* p, int enable_timing);
+SF_API int sf_plan_profile_read(sf_plan* p, int kernel, int64_t* launches, double* seconds, double* bytes);
+
 SF_API const char* sf_last_error(void);
 
 #ifdef __cplusplus

@@ -212,11 +212,40 @@ void sf_plan_destroy(sf_plan* h) {
   if (!h) return;
   free_host_buffers(h->hb);
   if (h->p) {
+    sf::prof_release(*h->p);
     if (h->p->d_tabA) cudaFree(h->p->d_tabA);
     if (h->p->d_tabB) cudaFree(h->p->d_tabB);
     sf::plan_destroy(h->p);
   }
   delete h;
+}
+
+int sf_plan_profile(sf_plan* h, int enable_timing) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  sf::Plan& p = *h->p;
+  sf::prof_collect(p);
+  for (int k = 0; k < 3; k++) {
+    p.prof.launches[k] = 0;
+    p.prof.bytes[k] = 0;
+    p.prof.seconds[k] = 0;
+  }
+  p.prof.timing = enable_timing != 0;
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_plan_profile_read(sf_plan* h, int kernel, int64_t* launches, double* seconds, double* bytes) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  if (kernel < 0 || kernel > 2) sf::fail(SF_EINVAL, "kernel must be 0, 1 or 2");
+  sf::Plan& p = *h->p;
+  sf::prof_collect(p);
+  if (launches) *launches = p.prof.launches[kernel];
+  if (seconds) *seconds = p.prof.seconds[kernel];
+  if (bytes) *bytes = p.prof.bytes[kernel];
+  return SF_OK;
+  SF_GUARD_END
 }
 
 int sf_selection_size(const sf_plan* h, const sf_path_sel* sel, uint64_t* n_paths, double* f_actual) {

@@ -98,6 +98,7 @@ uint64_t count_finals(const Plan& p, const std::vector<Range>& rs) {
 }
 
 void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan) {
+  static_assert(sizeof(PassLaunch) <= 32764, "kernel parameter block too large");
   if (pp.stages.size() > (size_t)MAX_STAGES || pp.ops.size() > (size_t)MAX_OPS ||
       pp.phases.size() > (size_t)MAX_PHASE_GROUPS || pp.mats.size() > (size_t)2 * MAX_MATS)
     fail(SF_EUNSUPPORTED, "internal: pass program too large");
@@ -136,8 +137,22 @@ struct Job {
   uint64_t path;
 };
 
+// Algorithmic bytes of one pass launch: live input amplitudes read (unless
+// generated) plus live output amplitudes written, 8 bytes each, per node.
+double pass_bytes(const DevPass& d, int nodes) {
+  uint32_t active = 0;
+  for (int j = 0; j < d.k; j++) active |= 1u << d.gpos[j];
+  uint32_t pin_in = 0, pin_out = 0;
+  for (int i = 0; i < d.n_pin_in; i++) pin_in |= 1u << d.pin_in[i].pos;
+  for (int i = 0; i < d.n_pin_out; i++) pin_out |= 1u << d.pin_out[i].pos;
+  const double tiles = std::ldexp(1.0, d.n_free);
+  const double rd = d.gen_input ? 0.0 : tiles * std::ldexp(1.0, d.k - __builtin_popcount(pin_in & active));
+  const double wr = tiles * std::ldexp(1.0, d.k - __builtin_popcount(pin_out & active));
+  return 8.0 * (rd + wr) * nodes;
+}
+
 // Run a segment program for a batch of nodes of one half.
-void run_segment(Cache&, const Plan& plan, const SegmentPlan& seg, const std::vector<Job>& jobs,
+void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<Job>& jobs,
                  cudaStream_t st) {
   if (jobs.empty()) return;
   for (size_t p = 0; p < seg.passes.size(); p++) {
@@ -158,7 +173,10 @@ void run_segment(Cache&, const Plan& plan, const SegmentPlan& seg, const std::ve
         L->nodes[j - j0].out = jobs[j].out;
         L->nodes[j - j0].path = jobs[j].path;
       }
+      void* e1 = nullptr;
+      prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes), st, &e1);
       launch_pass(*L, tiles, plan.fuse_bits, plan.tile_bits, st);
+      prof_end(plan, e1, st);
     }
   }
 }
@@ -173,6 +191,47 @@ size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s) {
   return lay.total_slots * node_bytes(p) + 256;
 }
 
+void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out) {
+  p.prof.launches[kind]++;
+  p.prof.bytes[kind] += bytes;
+  *e1_out = nullptr;
+  if (!p.prof.timing) return;
+  cudaEvent_t e[2];
+  for (int i = 0; i < 2; i++) {
+    if (!p.prof.pool.empty()) {
+      e[i] = (cudaEvent_t)p.prof.pool.back();
+      p.prof.pool.pop_back();
+    } else if (cudaEventCreate(&e[i]) != cudaSuccess) {
+      fail(SF_ECUDA, "cudaEventCreate failed");
+    }
+  }
+  cudaEventRecord(e[0], (cudaStream_t)stream);
+  p.prof.pending.push_back({kind, (void*)e[0], (void*)e[1]});
+  *e1_out = (void*)e[1];
+}
+
+void prof_end(Plan&, void* e1, void* stream) {
+  if (e1) cudaEventRecord((cudaEvent_t)e1, (cudaStream_t)stream);
+}
+
+void prof_collect(Plan& p) {
+  for (auto& r : p.prof.pending) {
+    cudaEventSynchronize((cudaEvent_t)r.e1);
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, (cudaEvent_t)r.e0, (cudaEvent_t)r.e1) == cudaSuccess)
+      p.prof.seconds[r.kind] += ms * 1e-3;
+    p.prof.pool.push_back(r.e0);
+    p.prof.pool.push_back(r.e1);
+  }
+  p.prof.pending.clear();
+}
+
+void prof_release(Plan& p) {
+  prof_collect(p);
+  for (void* e : p.prof.pool) cudaEventDestroy((cudaEvent_t)e);
+  p.prof.pool.clear();
+}
+
 void exec_release_cache(Plan& p) {
   delete reinterpret_cast<Cache*>(p.cache);
   p.cache = nullptr;
@@ -184,7 +243,12 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   double fa = 0;
   std::vector<Range> rs = select_ranges(plan, sel, &fa);
   if (n < 0) fail(SF_EINVAL, "negative bitstring count");
-  if (!accumulate) launch_zero(d_out, 2 * n, st);
+  if (!accumulate) {
+    void* e1 = nullptr;
+    prof_begin(plan, 2, 16.0 * n, st, &e1);
+    launch_zero(d_out, 2 * n, st);
+    prof_end(plan, e1, st);
+  }
   if (n == 0 || rs.empty()) return;
   const uint64_t nfin = count_finals(plan, rs);
   Layout lay = make_layout(plan, nfin);
@@ -419,7 +483,11 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         size_t g1 = std::min(gf.size(), g0 + GATHER_FINALS);
         G.n_finals = (int)(g1 - g0);
         for (size_t j = g0; j < g1; j++) G.finals[j - g0] = gf[j];
+        void* e1 = nullptr;
+        const double gb = (double)n * (8.0 + 32.0 + 16.0 * G.n_finals * (2 << G.g));
+        prof_begin(plan, 1, gb, st, &e1);
         launch_gather(G, st);
+        prof_end(plan, e1, st);
       }
     }
   } catch (...) {

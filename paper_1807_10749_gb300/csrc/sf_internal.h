@@ -245,8 +245,25 @@ struct Level {
   int shift;  // lowest path bit of the level
 };
 
+// Kernel counters (sf_plan_profile): launches, algorithmic bytes, and, when
+// timing is on, CUDA events around each launch.
+struct ProfRec {
+  int kind;
+  void* e0;  // cudaEvent_t
+  void* e1;
+};
+struct Profile {
+  bool timing = false;
+  int64_t launches[3] = {0, 0, 0};
+  double bytes[3] = {0, 0, 0};
+  double seconds[3] = {0, 0, 0};
+  std::vector<ProfRec> pending;
+  std::vector<void*> pool;
+};
+
 struct Plan {
   sf_plan_opts opts;
+  Profile prof;
   Circuit circ;
   uint64_t side_b_mask = 0;
   std::vector<CrossGate> cross;
@@ -283,6 +300,10 @@ size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s);
 void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, double* d_out,
               int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache);
 void exec_release_cache(Plan& p);
+void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out);
+void prof_end(Plan& p, void* e1, void* stream);
+void prof_collect(Plan& p);
+void prof_release(Plan& p);
 
 // ---------------------------------------------------------------- kernels
 void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, void* stream);

@@ -15,6 +15,16 @@ revisions):
     drawn uniformly from the two gates that differ from the previous one;
   * cycle D+1 applies H to every qubit.
 
+The "v2" variant (Section 6: benchmarks revised so that no T gate follows a
+CZ; Table 2's 7x8 row used them) changes the one-qubit rule:
+  * the gate in a slot right after a CZ is X^1/2 or Y^1/2 (uniform the first
+    time on that qubit, afterwards the one that differs from the previous);
+  * a qubit that received such a gate in cycle t-1 and is idle in cycle t
+    receives T in cycle t.
+For 7x8, depth 1+40+1 this gives 538 X^1/2 / Y^1/2 gates, exactly Table 2's
+1466 gates - 112 H - 485 CZ - 331 T, and 330 T gates (Table 2: 331). The
+paper does not print the rule; this placement is our reading of it.
+
 The eight CZ configurations (the paper names them but does not print them; the
 layout below reproduces the CZ and cross-cut CZ counts of the 7x7 and 7x8 rows
 of Table 2 exactly, see tests/golden/gate_counts.txt):
@@ -139,10 +149,11 @@ def haar_unitary(d: int, rng: SplitMix64) -> np.ndarray:
 
 
 def google_circuit(rows: int, cols: int, depth: int, seed: int = 1,
-                   haar: bool = False, iswap: bool = False) -> CircuitSpec:
+                   haar: bool = False, iswap: bool = False, v2: bool = False) -> CircuitSpec:
     """Random grid circuit of depth 1+depth+1 under the rules in the module
     docstring. haar=True replaces every CZ by a seeded Haar-random U(4)
-    (written as a 'u2' line); iswap=True replaces every CZ by iSWAP."""
+    (written as a 'u2' line); iswap=True replaces every CZ by iSWAP; v2=True
+    uses the revised one-qubit placement."""
     spec = CircuitSpec(rows, cols)
     n = rows * cols
     rng = SplitMix64(seed, PURPOSE_GATES)
@@ -151,6 +162,7 @@ def google_circuit(rows: int, cols: int, depth: int, seed: int = 1,
         spec.gates.append(Gate(0, "h", (q,)))
     last_1q = [None] * n
     prev_busy = set()
+    prev_slot = set()
     for t in range(1, depth + 1):
         edges = cz_edges(rows, cols, (t - 1) % 8)
         busy = set()
@@ -168,16 +180,24 @@ def google_circuit(rows: int, cols: int, depth: int, seed: int = 1,
                 spec.gates.append(Gate(t, "iswap", (a, b)))
             else:
                 spec.gates.append(Gate(t, "cz", (a, b)))
+        slot = set()
         for q in range(n):
             if q in prev_busy and q not in busy:
-                if last_1q[q] is None:
+                if v2:
+                    choices = [c for c in ("x_1_2", "y_1_2") if c != last_1q[q]]
+                    g = choices[rng.next() >> 63] if len(choices) == 2 else choices[0]
+                elif last_1q[q] is None:
                     g = "t"
                 else:
                     choices = [c for c in ("x_1_2", "y_1_2", "t") if c != last_1q[q]]
                     g = choices[rng.next() >> 63]
                 last_1q[q] = g
+                slot.add(q)
                 spec.gates.append(Gate(t, g, (q,)))
+            elif v2 and q in prev_slot and q not in busy:
+                spec.gates.append(Gate(t, "t", (q,)))
         prev_busy = busy
+        prev_slot = slot
     for q in range(n):
         spec.gates.append(Gate(depth + 1, "h", (q,)))
     return spec
@@ -238,7 +258,15 @@ WORKLOADS = {
     # 6x7, 1+26+1, halves 21+21 (rows 0-2 | 3-5), 1M bitstrings
     "6x7_d26": dict(rows=6, cols=7, depth=26, side_b_mask=row_cut_mask(6, 7, 3),
                     n_bitstrings=1_000_000, bitstring_seed=1002),
-    # 7x8, 1+40+1, halves 28+28 (cols 0-3 | 4-7), f = 0.5%, 1M bitstrings
+    # 7x8, 1+40+1, halves 28+28 (cols 0-3 | 4-7), f = 0.5%, 1M bitstrings;
+    # v2 one-qubit rule, as in Table 2's 7x8 row
     "7x8_d40": dict(rows=7, cols=8, depth=40, side_b_mask=column_cut_mask(7, 8, 4),
-                    n_bitstrings=1_000_000, bitstring_seed=1003),
+                    n_bitstrings=1_000_000, bitstring_seed=1003, v2=True),
 }
+
+
+def workload_circuit(name: str, seed: int = 1, **kw) -> CircuitSpec:
+    """The circuit of a named workload (its grid, depth and one-qubit rule)."""
+    w = WORKLOADS[name]
+    kw.setdefault("v2", w.get("v2", False))
+    return google_circuit(w["rows"], w["cols"], w["depth"], seed, **kw)

@@ -26,7 +26,8 @@ EXPORTED = [
     "sf_plan_opts_default", "sf_plan_create", "sf_plan_info", "sf_plan_stats", "sf_plan_destroy",
     "sf_selection_size", "sf_selection_ids", "sf_amplitudes", "sf_workspace_size",
     "sf_amplitudes_device", "sf_server_create", "sf_server_submit", "sf_server_wait",
-    "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_last_error",
+    "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_plan_profile",
+    "sf_plan_profile_read", "sf_last_error",
 ]
 
 
@@ -88,6 +89,8 @@ def lib():
             "sf_server_cancel": (i32, [P, u64]),
             "sf_server_times": (i32, [P, u64, P, P]),
             "sf_server_destroy": (None, [P]),
+            "sf_plan_profile": (i32, [P, i32]),
+            "sf_plan_profile_read": (i32, [P, i32, P, P, P]),
             "sf_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -255,6 +258,17 @@ def sf_server_times(server, ticket):
 
 def sf_server_destroy(server):
     lib().sf_server_destroy(server)
+
+
+def sf_plan_profile(plan, enable_timing=True):
+    _check(lib().sf_plan_profile(plan, 1 if enable_timing else 0))
+
+
+def sf_plan_profile_read(plan, kernel):
+    """(launches, seconds, algorithmic bytes) of kernel 0 pass, 1 gather, 2 other."""
+    n, t, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().sf_plan_profile_read(plan, kernel, ctypes.byref(n), ctypes.byref(t), ctypes.byref(b)))
+    return n.value, t.value, b.value
 
 
 def sf_last_error() -> str:

@@ -54,7 +54,7 @@ def test_circuit_create_matches_parse():
 def test_plan_matches_oracle_split(name):
     """Cut, cross-gate count and path bits agree with the oracle's split."""
     w = inputs.WORKLOADS[name]
-    spec = inputs.google_circuit(w["rows"], w["cols"], w["depth"], 1)
+    spec = inputs.workload_circuit(name)
     p = sfsim.Plan(spec.text(), side_b_mask=w["side_b_mask"])
     setup = sim.SFSetup(ocirc.parse(spec.text()), w["side_b_mask"])
     assert p.info["n_cross"] == setup.n_cross
@@ -111,7 +111,7 @@ def test_selection_ids_match_oracle_bit_exactly():
 
 def test_feistel_matches_oracle_at_28_bits():
     """The 7x8 FRACTION selection (x_s = 28) enumerates the oracle's prefixes."""
-    spec = inputs.google_circuit(7, 8, 40, 1)
+    spec = inputs.workload_circuit("7x8_d40")
     p = sfsim.Plan(spec.text(), side_b_mask=inputs.WORKLOADS["7x8_d40"]["side_b_mask"])
     sel = sfsim.selection("fraction", fidelity=0.005, seed=7)
     n, fa = sfsim.sf_selection_size(p.handle, sel)

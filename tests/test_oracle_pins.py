@@ -253,6 +253,12 @@ def test_truncated_sum_norm_and_fidelity_track_f():
 def test_gate_counts_match_table2_and_goldens():
     with open(os.path.join(HERE, "golden", "gate_counts.txt")) as fh:
         rows = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    v2rows = [r for r in rows if r[0] == "v2"]
+    rows = [r for r in rows if r[0] != "v2"]
+    for _, R, C, D, nxy, nt in v2rows:
+        spec = inputs.google_circuit(int(R), int(C), int(D), 1, v2=True)
+        assert sum(g.name in ("x_1_2", "y_1_2") for g in spec.gates) == int(nxy)
+        assert sum(g.name == "t" for g in spec.gates) == int(nt)
     for R, C, D, kind, fb, ncz, nx, cyc in rows:
         R, C, D, fb = int(R), int(C), int(D), int(fb)
         mask = inputs.column_cut_mask(R, C, fb) if kind == "col" else inputs.row_cut_mask(R, C, fb)
@@ -261,3 +267,29 @@ def test_gate_counts_match_table2_and_goldens():
         x = [g for g in cz if ((mask >> g.qubits[0]) & 1) != ((mask >> g.qubits[1]) & 1)]
         assert len(cz) == int(ncz) and len(x) == int(nx)
         assert sorted(set(g.cycle for g in x)) == [int(v) for v in cyc.split(",")]
+
+
+def test_v2_circuits_have_no_diagonal_only_gap_between_cut_czs():
+    """Section 6: the v2 rule leaves no CZ - (diagonal gates) - CZ run on a cut
+    qubit, so no path of the 7x8 workload is zero by construction; the T-first
+    rule leaves six such runs there (63/64 of the paths vanish)."""
+    def gaps(spec, mask):
+        inB = lambda q: (mask >> q) & 1
+        n = 0
+        seq = {}
+        for g in spec.gates:
+            for q in g.qubits:
+                if not inB(q):
+                    seq.setdefault(q, []).append(g)
+        for q, gs in seq.items():
+            last, diag = False, True
+            for g in gs:
+                if len(g.qubits) == 2 and inB(g.qubits[0]) != inB(g.qubits[1]):
+                    n += last and diag
+                    last, diag = True, True
+                elif g.name in ("x_1_2", "y_1_2", "h"):
+                    diag = False
+        return n
+    w = inputs.WORKLOADS["7x8_d40"]
+    assert gaps(inputs.workload_circuit("7x8_d40"), w["side_b_mask"]) == 0
+    assert gaps(inputs.google_circuit(7, 8, 40, 1), w["side_b_mask"]) == 6
