@@ -8,23 +8,7 @@
 
 #include "sf_internal.h"
 
-struct sf_circuit {
-  sf::Circuit c;
-};
-
-struct HostBuffers {
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  uint64_t* bits = nullptr;
-  double* out = nullptr;
-  int64_t cap_n = 0;
-  cudaStream_t stream = nullptr;
-};
-
-struct sf_plan {
-  sf::Plan* p = nullptr;
-  HostBuffers hb;
-};
+using HostBuffers = SfHostBuffers;
 
 namespace sf {
 
@@ -62,6 +46,39 @@ static void cuda_check(cudaError_t e, const char* what) {
   if (e != cudaSuccess) sf::fail(e == cudaErrorMemoryAllocation ? SF_ENOMEM : SF_ECUDA,
                                  std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// Device-side state of a plan, created on first use (plan creation itself
+// makes no CUDA call): the gather byte tables and the memory budget.
+namespace sf {
+void ensure_device(sf::Plan& p) {
+  if (p.d_tabA) return;
+  cuda_check(cudaGetDevice(&p.device), "cudaGetDevice");
+  if (p.opts.hbm_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cuda_check(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+    p.opts.hbm_budget_bytes = (int64_t)(fr / 4 * 3);
+  }
+  uint32_t *a = nullptr, *b = nullptr;
+  int* e = nullptr;
+  try {
+    cuda_check(cudaMalloc(&e, sizeof(int)), "cudaMalloc");
+    cuda_check(cudaMemset(e, 0, sizeof(int)), "cudaMemset");
+    cuda_check(cudaMalloc(&a, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
+    cuda_check(cudaMalloc(&b, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
+    cuda_check(cudaMemcpy(a, p.A.tab.data(), 8 * 256 * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+    cuda_check(cudaMemcpy(b, p.B.tab.data(), 8 * 256 * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
+  } catch (...) {
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (e) cudaFree(e);
+    throw;
+  }
+  p.d_err = e;
+  p.d_tabA = a;
+  p.d_tabB = b;
+}
+}  // namespace sf
+using sf::ensure_device;
 
 extern "C" {
 
@@ -175,36 +192,13 @@ int sf_plan_stats(const sf_plan* h, int* passes_a, int* passes_b, int* stages_a,
   SF_GUARD_END
 }
 
-// Device-side state of a plan, created on first use (plan creation itself
-// makes no CUDA call): the gather byte tables and the memory budget.
-static void ensure_device(sf::Plan& p) {
-  if (p.d_tabA) return;
-  cuda_check(cudaGetDevice(&p.device), "cudaGetDevice");
-  if (p.opts.hbm_budget_bytes == 0) {
-    size_t fr = 0, tot = 0;
-    cuda_check(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-    p.opts.hbm_budget_bytes = (int64_t)(fr / 4 * 3);
-  }
-  uint32_t *a = nullptr, *b = nullptr;
-  try {
-    cuda_check(cudaMalloc(&a, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
-    cuda_check(cudaMalloc(&b, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
-    cuda_check(cudaMemcpy(a, p.A.tab.data(), 8 * 256 * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
-    cuda_check(cudaMemcpy(b, p.B.tab.data(), 8 * 256 * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
-  } catch (...) {
-    if (a) cudaFree(a);
-    if (b) cudaFree(b);
-    throw;
-  }
-  p.d_tabA = a;
-  p.d_tabB = b;
-}
+
 
 static void free_host_buffers(HostBuffers& hb) {
   if (hb.ws) cudaFree(hb.ws);
   if (hb.bits) cudaFree(hb.bits);
   if (hb.out) cudaFree(hb.out);
-  if (hb.stream) cudaStreamDestroy(hb.stream);
+  if (hb.stream) cudaStreamDestroy((cudaStream_t)hb.stream);
   hb = HostBuffers();
 }
 
@@ -213,6 +207,7 @@ void sf_plan_destroy(sf_plan* h) {
   free_host_buffers(h->hb);
   if (h->p) {
     sf::prof_release(*h->p);
+    if (h->p->d_err) cudaFree(h->p->d_err);
     if (h->p->d_tabA) cudaFree(h->p->d_tabA);
     if (h->p->d_tabB) cudaFree(h->p->d_tabB);
     sf::plan_destroy(h->p);
@@ -310,7 +305,12 @@ int sf_amplitudes(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel
   HostBuffers& hb = h->hb;
   ensure_device(*h->p);
   size_t need = sf::exec_workspace_bytes(*h->p, n, *sel);
-  if (!hb.stream) cuda_check(cudaStreamCreateWithFlags(&hb.stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (!hb.stream) {
+    cudaStream_t st = nullptr;
+    cuda_check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
+    hb.stream = st;
+  }
+  cudaStream_t hst = (cudaStream_t)hb.stream;
   if (hb.ws_bytes < need) {
     if (hb.ws) cudaFree(hb.ws);
     hb.ws = nullptr;
@@ -328,10 +328,13 @@ int sf_amplitudes(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel
     cuda_check(cudaMalloc(&hb.out, (size_t)n * 16), "cudaMalloc output");
     hb.cap_n = n;
   }
-  cuda_check(cudaMemcpyAsync(hb.bits, bits, (size_t)n * 8, cudaMemcpyHostToDevice, hb.stream), "cudaMemcpyAsync");
-  sf::exec_run(*h->p, hb.bits, n, *sel, hb.out, 0, hb.ws, hb.ws_bytes, hb.stream, true);
-  cuda_check(cudaMemcpyAsync(out, hb.out, (size_t)n * 16, cudaMemcpyDeviceToHost, hb.stream), "cudaMemcpyAsync");
-  cuda_check(cudaStreamSynchronize(hb.stream), "cudaStreamSynchronize");
+  cuda_check(cudaMemcpyAsync(hb.bits, bits, (size_t)n * 8, cudaMemcpyHostToDevice, hst), "cudaMemcpyAsync");
+  sf::exec_run(*h->p, hb.bits, n, *sel, hb.out, 0, hb.ws, hb.ws_bytes, hst, true);
+  cuda_check(cudaMemcpyAsync(out, hb.out, (size_t)n * 16, cudaMemcpyDeviceToHost, hst), "cudaMemcpyAsync");
+  cuda_check(cudaStreamSynchronize(hst), "cudaStreamSynchronize");
+  int flag = 0;
+  cuda_check(cudaMemcpy(&flag, h->p->d_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+  if (flag) sf::fail(SF_ECUDA, "a kernel wait timed out (error flag set); results are invalid");
   return SF_OK;
   SF_GUARD_END
 }

@@ -103,6 +103,7 @@ void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan) {
       pp.phases.size() > (size_t)MAX_PHASE_GROUPS || pp.mats.size() > (size_t)2 * MAX_MATS)
     fail(SF_EUNSUPPORTED, "internal: pass program too large");
   L.pass = pp.dev;
+  L.err = plan.d_err;
   std::copy(pp.stages.begin(), pp.stages.end(), L.stages);
   std::copy(pp.ops.begin(), pp.ops.end(), L.ops);
   std::copy(pp.phases.begin(), pp.phases.end(), L.phases);
@@ -153,7 +154,7 @@ double pass_bytes(const DevPass& d, int nodes) {
 
 // Run a segment program for a batch of nodes of one half.
 void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<Job>& jobs,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool prof) {
   if (jobs.empty()) return;
   for (size_t p = 0; p < seg.passes.size(); p++) {
     const PassPlan& pp = seg.passes[p];
@@ -174,9 +175,9 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
         L->nodes[j - j0].path = jobs[j].path;
       }
       void* e1 = nullptr;
-      prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes), st, &e1);
+      if (prof) prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes), st, &e1);
       launch_pass(*L, tiles, plan.fuse_bits, plan.tile_bits, st);
-      prof_end(plan, e1, st);
+      if (prof) prof_end(plan, e1, st);
     }
   }
 }
@@ -237,17 +238,23 @@ void exec_release_cache(Plan& p) {
   p.cache = nullptr;
 }
 
+void exec_free_cache(void* c) { delete reinterpret_cast<Cache*>(c); }
+
 void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& sel, double* d_out,
-              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache) {
+              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
+              ExecCtx* ctx) {
   cudaStream_t st = (cudaStream_t)stream;
+  void** cache_slot = (ctx && ctx->cache_slot) ? ctx->cache_slot : &plan.cache;
+  const bool prof = ctx ? ctx->profile : true;
+  const volatile int* cancel = ctx ? ctx->cancel : nullptr;
   double fa = 0;
   std::vector<Range> rs = select_ranges(plan, sel, &fa);
   if (n < 0) fail(SF_EINVAL, "negative bitstring count");
   if (!accumulate) {
     void* e1 = nullptr;
-    prof_begin(plan, 2, 16.0 * n, st, &e1);
+    if (prof) prof_begin(plan, 2, 16.0 * n, st, &e1);
     launch_zero(d_out, 2 * n, st);
-    prof_end(plan, e1, st);
+    if (prof) prof_end(plan, e1, st);
   }
   if (n == 0 || rs.empty()) return;
   const uint64_t nfin = count_finals(plan, rs);
@@ -258,11 +265,11 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
     fail(SF_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~(uintptr_t)255);
 
-  Cache* C = reinterpret_cast<Cache*>(plan.cache);
+  Cache* C = reinterpret_cast<Cache*>(*cache_slot);
   if (!C || !keep_cache || C->ws != ws || C->ws_bytes != ws_bytes || C->B != lay.B || C->cap != lay.cap) {
     delete C;
     C = new Cache();
-    plan.cache = C;
+    *cache_slot = C;
     C->ws = ws;
     C->ws_bytes = ws_bytes;
     C->B = lay.B;
@@ -361,6 +368,7 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
     Final f;
     bool more = next_final(f);
     while (more) {
+      if (cancel && *cancel) fail(SF_ECANCELLED, "request cancelled");
       block.clear();
       while (more && (int)block.size() < lay.B) {
         block.push_back(f);
@@ -435,8 +443,8 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
           }
           computed.push_back(freep);
         }
-        run_segment(*C, plan, plan.A.seg[s], jobsA, st);
-        run_segment(*C, plan, plan.B.seg[s], jobsB, st);
+        run_segment(*C, plan, plan.A.seg[s], jobsA, st, prof);
+        run_segment(*C, plan, plan.B.seg[s], jobsB, st, prof);
         for (size_t q : computed) slots[q].valid = true;
         prev_ids = ids;
         prev_slot = where;
@@ -477,17 +485,17 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         std::memcpy(g.leafmask, block[i].mask, sizeof(g.leafmask));
         gf.push_back(g);
       }
-      run_segment(*C, plan, finA, jobsA, st);
-      run_segment(*C, plan, finB, jobsB, st);
+      run_segment(*C, plan, finA, jobsA, st, prof);
+      run_segment(*C, plan, finB, jobsB, st, prof);
       for (size_t g0 = 0; g0 < gf.size(); g0 += GATHER_FINALS) {
         size_t g1 = std::min(gf.size(), g0 + GATHER_FINALS);
         G.n_finals = (int)(g1 - g0);
         for (size_t j = g0; j < g1; j++) G.finals[j - g0] = gf[j];
         void* e1 = nullptr;
         const double gb = (double)n * (8.0 + 32.0 + 16.0 * G.n_finals * (2 << G.g));
-        prof_begin(plan, 1, gb, st, &e1);
+        if (prof) prof_begin(plan, 1, gb, st, &e1);
         launch_gather(G, st);
-        prof_end(plan, e1, st);
+        if (prof) prof_end(plan, e1, st);
       }
     }
   } catch (...) {

@@ -20,6 +20,7 @@
 //                  closed form when the planner deferred it; FP64 accumulation.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 
 #include "sf_internal.h"
@@ -248,76 +249,115 @@ __device__ __forceinline__ uint32_t pin_val(const DevPin& p, const uint8_t* xshi
 
 }  // namespace
 
-template <int R>
-__global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PassLaunch P) {
-  extern __shared__ float4 smem_raw[];
-  float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const DevPass& d = P.pass;
-  const int k = d.k, L = d.L;
-  const int ntile = 1 << k;
-  uint32_t* runoff = reinterpret_cast<uint32_t*>(sm + ntile);
-  __shared__ float2 w8[8];
-  const int node = blockIdx.y;
-  const uint64_t path = P.nodes[node].path;
-
-  uint32_t base = 0;
-  {
-    const uint32_t t = blockIdx.x;
-    for (int i = 0; i < d.n_free; i++) base |= ((t >> i) & 1u) << d.freepos[i];
+// ---- TMA bulk copies and mbarriers (inline PTX) ---------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Wait for phase `parity` of the barrier, giving up after ~2^31 cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
   }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Per-item geometry: tile base index and pin masks (tile-local and run-level).
+struct ItemGeo {
+  uint32_t base;                 // global index bits of the tile (inactive bits)
+  uint32_t lin_m, lin_v;         // input pins on tile-local bits
+  uint32_t lout_m, lout_v;       // output pins on tile-local bits
+  int node;
+  uint64_t path;
+};
+
+__device__ __forceinline__ ItemGeo item_geo(const PassLaunch& P, int64_t item, int tiles_log2) {
+  const DevPass& d = P.pass;
+  ItemGeo g;
+  g.node = (int)(item >> tiles_log2);
+  const uint32_t t = (uint32_t)(item & ((1ll << tiles_log2) - 1));
+  g.path = P.nodes[g.node].path;
+  uint32_t base = 0;
+  for (int i = 0; i < d.n_free; i++) base |= ((t >> i) & 1u) << d.freepos[i];
   uint32_t active = 0;
-  for (int j = 0; j < k; j++) active |= 1u << d.gpos[j];
-  uint32_t pin_mask = 0, pin_val_g = 0;
+  for (int j = 0; j < d.k; j++) active |= 1u << d.gpos[j];
+  uint32_t pm = 0, pv = 0, om = 0, ov = 0;
   for (int i = 0; i < d.n_pin_in; i++) {
     const uint32_t b = 1u << d.pin_in[i].pos;
-    pin_mask |= b;
-    if (pin_val(d.pin_in[i], P.xshift, P.xbits, path)) pin_val_g |= b;
+    pm |= b;
+    if (pin_val(d.pin_in[i], P.xshift, P.xbits, g.path)) pv |= b;
   }
-  uint32_t pout_mask = 0, pout_val = 0;
   for (int i = 0; i < d.n_pin_out; i++) {
     const uint32_t b = 1u << d.pin_out[i].pos;
-    pout_mask |= b;
-    if (pin_val(d.pin_out[i], P.xshift, P.xbits, path)) pout_val |= b;
+    om |= b;
+    if (pin_val(d.pin_out[i], P.xshift, P.xbits, g.path)) ov |= b;
   }
-  base |= pin_val_g & ~active;
-  uint32_t lin_m = 0, lin_v = 0, lout_m = 0, lout_v = 0;
-  for (int j = 0; j < k; j++) {
+  g.base = base | (pv & ~active);
+  g.lin_m = g.lin_v = g.lout_m = g.lout_v = 0;
+  for (int j = 0; j < d.k; j++) {
     const uint32_t gb = 1u << d.gpos[j];
-    if (pin_mask & gb) {
-      lin_m |= 1u << j;
-      if (pin_val_g & gb) lin_v |= 1u << j;
+    if (pm & gb) {
+      g.lin_m |= 1u << j;
+      if (pv & gb) g.lin_v |= 1u << j;
     }
-    if (pout_mask & gb) {
-      lout_m |= 1u << j;
-      if (pout_val & gb) lout_v |= 1u << j;
+    if (om & gb) {
+      g.lout_m |= 1u << j;
+      if (ov & gb) g.lout_v |= 1u << j;
     }
   }
-  if (threadIdx.x < 8) {
-    const float r = 0.70710678118654752f;
-    const float2 t8[8] = {{1.f, 0.f}, {r, r}, {0.f, 1.f}, {-r, r}, {-1.f, 0.f}, {-r, -r}, {0.f, -1.f}, {r, -r}};
-    w8[threadIdx.x] = t8[threadIdx.x];
-  }
-  const int nruns = 1 << (k - L);
-  for (int rI = threadIdx.x; rI < nruns; rI += blockDim.x) {
-    uint32_t hi = 0;
-    for (int j = L; j < k; j++) hi |= (uint32_t)((rI >> (j - L)) & 1) << d.gpos[j];
-    runoff[rI] = hi;
-  }
-  __syncthreads();
+  return g;
+}
 
-  // ---- load the tile (global -> shared), zero outside the input pins ----
-  const float2* in = reinterpret_cast<const float2*>(P.nodes[node].in);
-  const int lmask = (1 << L) - 1;
-  for (int e = threadIdx.x; e < ntile; e += blockDim.x) {
-    const int off = e & lmask;
-    const uint32_t g = base | runoff[e >> L] | (uint32_t)off;
-    float2 val = make_float2(0.f, 0.f);
-    if (((uint32_t)e & lin_m) == lin_v) val = d.gen_input ? make_float2(1.f, 0.f) : in[g];
-    sm[e] = val;
+// Issue the TMA loads of one item's live runs into buffer `dst` (warp 0).
+__device__ __forceinline__ void issue_loads(const PassLaunch& P, const ItemGeo& g, const uint32_t* runoff,
+                                            uint32_t dst, uint32_t bar, int lane) {
+  const DevPass& d = P.pass;
+  const int L = d.L, nruns = 1 << (d.k - L);
+  const uint32_t rm = g.lin_m >> L, rv = g.lin_v >> L;
+  const uint32_t run_bytes = 8u << L;
+  if (lane == 0) {
+    const uint32_t live = d.gen_input ? 0u : ((uint32_t)nruns >> __popc(rm));
+    mbar_arrive_tx(bar, live * run_bytes);
   }
-  __syncthreads();
+  __syncwarp();
+  if (d.gen_input) return;
+  const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
+  for (int r = lane; r < nruns; r += 32) {
+    if (((uint32_t)r & rm) != rv) continue;
+    bulk_g2s(dst + (uint32_t)r * run_bytes, in + (g.base | runoff[r]), run_bytes, bar);
+  }
+}
 
-  // ---- register stages ----
+template <int R>
+__device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
+                                           float post_scale) {
+  const DevPass& d = P.pass;
+  const int k = d.k;
   for (int s = 0; s < d.n_stages; s++) {
     const DevStage& st = P.stages[s];
     int roff[R], gr[R];
@@ -328,7 +368,6 @@ __global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PassL
       gr[j] = d.gpos[st.rbit[j]];
       rl |= 1u << st.rbit[j];
     }
-    // thread's fixed local bits: threadIdx bits deposited into non-register bits
     uint32_t lfix = 0;
     {
       uint32_t t = threadIdx.x;
@@ -338,7 +377,7 @@ __global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PassL
         t >>= 1;
       }
     }
-    uint32_t gfix = base;
+    uint32_t gfix = g.base;
     for (int j = 0; j < k; j++)
       if ((lfix >> j) & 1u) gfix |= 1u << d.gpos[j];
     float2 v[1 << R];
@@ -368,7 +407,7 @@ __global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PassL
           break;
         }
         case DOP_G1SEL: {
-          const int dg = digit_of(P.xshift, P.xbits, path, op.xi);
+          const int dg = digit_of(P.xshift, P.xbits, g.path, op.xi);
           const float* m = P.mats + 2 * (op.arg + 4 * dg);
           dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
                          make_float2(m[4], m[5]), make_float2(m[6], m[7]));
@@ -378,7 +417,7 @@ __global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PassL
           dispatch_g2<R>(op.a, op.b, v, P.mats + 2 * op.arg);
           break;
         case DOP_PHASE:
-          apply_phase<R>(P.phases[op.arg], v, gfix, gr, P.xshift, P.xbits, path, w8);
+          apply_phase<R>(P.phases[op.arg], v, gfix, gr, P.xshift, P.xbits, g.path, w8);
           break;
         case DOP_DMUL: {
           const float* m = P.mats + 2 * op.arg;
@@ -400,30 +439,116 @@ __global__ void __launch_bounds__(512) pass_kernel(const __grid_constant__ PassL
           break;
       }
     }
+    const float sc = (s == d.n_stages - 1) ? post_scale : 1.0f;
     {
       int addr = (int)lfix;
-      sm[addr] = v[0];
+      sm[addr] = make_float2(v[0].x * sc, v[0].y * sc);
 #pragma unroll
       for (int i = 1; i < (1 << R); i++) {
         const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
         const int j = cctz(gi ^ prev);
         addr += (gi & (1 << j)) ? roff[j] : -roff[j];
-        sm[addr] = v[gi];
+        sm[addr] = make_float2(v[gi].x * sc, v[gi].y * sc);
       }
     }
     __syncthreads();
   }
+}
 
-  // ---- store the tile (shared -> global), skipping pinned-out positions ----
-  float2* out = reinterpret_cast<float2*>(P.nodes[node].out);
-  const float sc = d.post_scale;
-  for (int e = threadIdx.x; e < ntile; e += blockDim.x) {
-    if (((uint32_t)e & lout_m) != lout_v) continue;
-    const int off = e & lmask;
-    const uint32_t g = base | runoff[e >> L] | (uint32_t)off;
-    float2 val = sm[e];
-    out[g] = make_float2(val.x * sc, val.y * sc);
+// Persistent fused pass. Each CTA walks work items (node, tile) with stride
+// gridDim.x; tiles move between global and shared memory as runs of 2^L
+// contiguous amplitudes with TMA bulk copies, double-buffered: the loads of
+// item i+2 run while item i+1 is computed. Input-pinned (structurally zero)
+// runs are never read and output-pinned runs never written.
+template <int R>
+__global__ void __launch_bounds__(256, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
+  constexpr int NBUF = 2;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const DevPass& d = P.pass;
+  const int k = d.k, L = d.L;
+  const int ntile = 1 << k, nruns = 1 << (k - L);
+  float2* bufs = reinterpret_cast<float2*>(smem);
+  uint32_t* runoff = reinterpret_cast<uint32_t*>(bufs + NBUF * ntile);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(runoff + ((nruns + 1) & ~1));
+  __shared__ float2 w8[8];
+  const int tiles_log2 = d.n_free;
+  const int64_t items = (int64_t)P.n_nodes << tiles_log2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t run_bytes = 8u << L;
+
+  if (threadIdx.x < 8) {
+    const float r = 0.70710678118654752f;
+    const float2 t8[8] = {{1.f, 0.f}, {r, r}, {0.f, 1.f}, {-r, r}, {-1.f, 0.f}, {-r, -r}, {0.f, -1.f}, {r, -r}};
+    w8[threadIdx.x] = t8[threadIdx.x];
   }
+  for (int rI = threadIdx.x; rI < nruns; rI += blockDim.x) {
+    uint32_t hi = 0;
+    for (int j = L; j < k; j++) hi |= (uint32_t)((rI >> (j - L)) & 1) << d.gpos[j];
+    runoff[rI] = hi;
+  }
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < NBUF; b++) mbar_init(smem_u32(&bars[b]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int b = 0; b < NBUF; b++) {
+      const int64_t it = blockIdx.x + (int64_t)b * gridDim.x;
+      if (it < items) issue_loads(P, item_geo(P, it, tiles_log2), runoff, smem_u32(bufs + b * ntile),
+                                  smem_u32(&bars[b]), lane);
+    }
+  }
+  int i = 0;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
+    const int b = i % NBUF;
+    const uint32_t parity = (uint32_t)((i / NBUF) & 1);
+    float2* sm = bufs + b * ntile;
+    const ItemGeo g = item_geo(P, it, tiles_log2);
+    const int timed_out = mbar_wait(smem_u32(&bars[b]), parity) ? 0 : 1;
+    if (__syncthreads_or(timed_out)) {
+      if (threadIdx.x == 0) atomicExch(P.err, 1);
+      break;
+    }
+    // generated input, or zeros at input-pinned positions
+    if (d.gen_input) {
+      for (int e = threadIdx.x; e < ntile; e += blockDim.x)
+        sm[e] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+      __syncthreads();
+    } else if (g.lin_m) {
+      for (int e = threadIdx.x; e < ntile; e += blockDim.x)
+        if (((uint32_t)e & g.lin_m) != g.lin_v) sm[e] = make_float2(0.f, 0.f);
+      __syncthreads();
+    }
+    run_stages<R>(P, sm, g, w8, d.post_scale);
+    if (d.n_stages == 0 && d.post_scale != 1.0f) {
+      for (int e = threadIdx.x; e < ntile; e += blockDim.x) {
+        float2 v = sm[e];
+        sm[e] = make_float2(v.x * d.post_scale, v.y * d.post_scale);
+      }
+      __syncthreads();
+    }
+    // shared -> global: the generic-proxy writes must be visible to the TMA
+    fence_async_smem();
+    __syncthreads();
+    if (warp == 0) {
+      float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
+      const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
+      const uint32_t src = smem_u32(sm);
+      for (int r = lane; r < nruns; r += 32) {
+        if (((uint32_t)r & rm) != rv) continue;
+        bulk_s2g(out + (g.base | runoff[r]), src + (uint32_t)r * run_bytes, run_bytes);
+      }
+      bulk_commit();
+      const int64_t nx = it + (int64_t)NBUF * gridDim.x;
+      if (nx < items) {
+        bulk_wait_read0();  // the stores have read this buffer
+        __syncwarp();
+        fence_async_smem();
+        issue_loads(P, item_geo(P, nx, tiles_log2), runoff, src, smem_u32(&bars[b]), lane);
+      }
+    }
+  }
+  if (warp == 0) bulk_wait0();
 }
 
 // ------------------------------------------------------------------ gather
@@ -575,15 +700,23 @@ static int num_sms() {
 template <int R>
 static void launch_pass_r(const PassLaunch& L, int tiles, int tile_k, cudaStream_t s) {
   const int threads = 1 << (tile_k - R);
-  const size_t smem = ((size_t)8 << tile_k) + ((size_t)4 << (tile_k - L.pass.L)) + 16;
+  const int nruns = 1 << (tile_k - L.pass.L);
+  const size_t smem = 2 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 2 * 8;
   static int configured[MAX_K + 1] = {0};
+  static int per_sm[MAX_K + 1] = {0};
   if (!configured[tile_k]) {
     check(cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
           "cudaFuncSetAttribute");
+    int nb = 0;
+    check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<R>, threads, smem),
+          "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    per_sm[tile_k] = nb > 0 ? nb : 1;
     configured[tile_k] = 1;
   }
-  dim3 grid(tiles, L.n_nodes);
-  pass_kernel<R><<<grid, threads, smem, s>>>(L);
+  const int64_t items = (int64_t)tiles * L.n_nodes;
+  int64_t grid = std::min<int64_t>(items, (int64_t)num_sms() * per_sm[tile_k]);
+  if (grid < 1) return;
+  pass_kernel<R><<<(int)grid, threads, smem, s>>>(L);
   check(cudaGetLastError(), "pass_kernel launch");
 }
 
@@ -591,7 +724,7 @@ void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, v
   cudaStream_t s = (cudaStream_t)stream;
   const int k = L.pass.k;
   const int R = L.pass.R;
-  if (k - R > 9 || k > MAX_K || R < 1) fail(SF_EINVAL, "internal: bad tile shape");
+  if (k - R > 8 || k > 13 || R < 1) fail(SF_EINVAL, "internal: bad tile shape");
   (void)fuse_bits;
   (void)tile_bits;
   switch (R) {

@@ -137,6 +137,7 @@ struct PassLaunch {
   float mats[2 * MAX_MATS];
   uint8_t xshift[MAX_CROSS];
   uint8_t xbits[MAX_CROSS];
+  int* err;        // set to 1 if a bounded wait gave up
   int32_t n_nodes;
   PassNode nodes[MAX_NODES];
 };
@@ -279,6 +280,7 @@ struct Plan {
   // device copies
   uint32_t* d_tabA = nullptr;
   uint32_t* d_tabB = nullptr;
+  int* d_err = nullptr;  // device error flag of bounded waits
   int device = 0;
   // executor cache (resident nodes between calls that reuse a workspace)
   void* cache = nullptr;
@@ -296,9 +298,20 @@ std::vector<Range> select_ranges(const Plan& p, const sf_path_sel& s, double* f_
 uint64_t feistel(uint64_t v, int w, uint64_t key);
 
 // -------------------------------------------------------------- executor
+// Per-call context: where the resident-node cache lives, whether launches are
+// counted in the plan's profile, and a cancellation flag checked between
+// path blocks. nullptr = the plan's own cache and profile, no cancellation.
+struct ExecCtx {
+  void** cache_slot = nullptr;
+  bool profile = true;
+  const volatile int* cancel = nullptr;
+};
 size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s);
 void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, double* d_out,
-              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache);
+              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
+              ExecCtx* ctx = nullptr);
+void exec_free_cache(void* cache);
+void ensure_device(Plan& p);
 void exec_release_cache(Plan& p);
 void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out);
 void prof_end(Plan& p, void* e1, void* stream);
@@ -311,3 +324,22 @@ void launch_gather(const GatherLaunch& L, void* stream);
 void launch_zero(double* p, int64_t n_doubles, void* stream);
 
 }  // namespace sf
+
+// Handle types of the C ABI (shared by capi.cpp and server.cpp).
+struct sf_circuit {
+  sf::Circuit c;
+};
+
+struct SfHostBuffers {  // device buffers of the host-pointer call, reused
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  uint64_t* bits = nullptr;
+  double* out = nullptr;
+  int64_t cap_n = 0;
+  void* stream = nullptr;  // cudaStream_t
+};
+
+struct sf_plan {
+  sf::Plan* p = nullptr;
+  SfHostBuffers hb;
+};
