@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "sf_internal.h"
 
@@ -687,7 +688,7 @@ static void check(cudaError_t e, const char* what) {
 }
 
 static int num_sms() {
-  static int n = 0;
+  static int n = 0;  // one device per process is assumed for the SM count
   if (!n) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -702,19 +703,29 @@ static void launch_pass_r(const PassLaunch& L, int tiles, int tile_k, cudaStream
   const int threads = 1 << (tile_k - R);
   const int nruns = 1 << (tile_k - L.pass.L);
   const size_t smem = 2 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 2 * 8;
-  static int configured[MAX_K + 1] = {0};
+  // The dynamic shared-memory limit is a property of the kernel function, so
+  // it only ever grows; occupancy is cached per tile size.
+  static std::mutex mu;
+  static size_t smem_set = 0;
   static int per_sm[MAX_K + 1] = {0};
-  if (!configured[tile_k]) {
-    check(cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-          "cudaFuncSetAttribute");
-    int nb = 0;
-    check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<R>, threads, smem),
-          "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    per_sm[tile_k] = nb > 0 ? nb : 1;
-    configured[tile_k] = 1;
+  int nb;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem > smem_set) {
+      check(cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+            "cudaFuncSetAttribute");
+      smem_set = smem;
+    }
+    if (!per_sm[tile_k]) {
+      int v = 0;
+      check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, pass_kernel<R>, threads, smem),
+            "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      per_sm[tile_k] = v > 0 ? v : 1;
+    }
+    nb = per_sm[tile_k];
   }
   const int64_t items = (int64_t)tiles * L.n_nodes;
-  int64_t grid = std::min<int64_t>(items, (int64_t)num_sms() * per_sm[tile_k]);
+  int64_t grid = std::min<int64_t>(items, (int64_t)num_sms() * nb);
   if (grid < 1) return;
   pass_kernel<R><<<(int)grid, threads, smem, s>>>(L);
   check(cudaGetLastError(), "pass_kernel launch");

@@ -262,6 +262,10 @@ WORKLOADS = {
     # v2 one-qubit rule, as in Table 2's 7x8 row
     "7x8_d40": dict(rows=7, cols=8, depth=40, side_b_mask=column_cut_mask(7, 8, 4),
                     n_bitstrings=1_000_000, bitstring_seed=1003, v2=True),
+    # profiling case: the same kernels on 25+25-qubit halves (256 MiB each,
+    # larger than L2) in a few GB of device memory
+    "5x10_d16": dict(rows=5, cols=10, depth=16, side_b_mask=column_cut_mask(5, 10, 5),
+                     n_bitstrings=100_000, bitstring_seed=1005, v2=True),
 }
 
 

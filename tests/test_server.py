@@ -64,11 +64,12 @@ def test_admission_by_footprint_and_latency(plans):
     bits = inputs.random_bitstrings(n, 1000, 3)
     sel = sfsim.selection("fraction", fidelity=1.0)
     ws = sfsim.sf_workspace_size(plan.handle, len(bits), sel)
+    one = ws + 24 * len(bits)
     # a budget that admits one such request at a time
-    srv = sfsim.sf_server_create(int(1.5 * (ws + 24 * len(bits))), 4)
+    srv = sfsim.sf_server_create(one + one // 2, 4)
     try:
+        big = inputs.random_bitstrings(n, one // 24, 4)   # its bitstrings alone exceed the rest
         with pytest.raises(sfsim.SFError) as e:
-            big = inputs.random_bitstrings(n, 10_000_000, 4)
             sfsim.sf_server_submit(srv, plan.handle, big, sel)
         assert e.value.code == sfsim.SF_ENOMEM
         ts = [sfsim.sf_server_submit(srv, plan.handle, bits, sel) for _ in range(3)]
