@@ -170,6 +170,28 @@ SF_API int sf_amplitudes_device(sf_plan* p, const uint64_t* d_bitstrings, int64_
                          double* d_out_amps, int accumulate, void* d_workspace, size_t ws_bytes,
                          void* cuda_stream);
 
+/* Fixed-scratch form of sf_amplitudes_device. This call has no counterpart
+ * in the paper; it exists for callers that must not allocate device memory
+ * once they run (cudaMalloc may synchronise the device, and fails when
+ * another allocator in the process already holds the free memory). All of its
+ * scratch - the path-tree node buffers, the gather tables and the wait error
+ * flag - lives in one array of SF_NOALLOC_SCRATCH_BYTES compiled into the
+ * library, which every GPU that loads the library keeps until process exit.
+ * Arguments are those of sf_amplitudes_device minus the workspace: d_bitstrings
+ * (n uint64) and d_out_amps (2n doubles, overwritten unless accumulate != 0)
+ * are caller-owned device buffers; the work is enqueued on cuda_stream.
+ * The call never calls cudaMalloc or cudaFree. Its first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. A plan whose one
+ * path needs more node memory than the array holds is rejected with SF_ENOMEM
+ * and a message. All calls share the one array, which keeps the previous
+ * call's contents; calls that can overlap on the GPU (other streams, other
+ * threads) race on it and must be serialised by the caller. */
+#define SF_NOALLOC_SCRATCH_BYTES (64ull << 20)
+SF_API int sf_amplitudes_device_noalloc(sf_plan* p, const uint64_t* d_bitstrings, int64_t n,
+                                        const sf_path_sel* sel, double* d_out_amps, int accumulate,
+                                        void* cuda_stream);
+
 /* Request server (continuous batching): requests are admitted while their
  * device footprint fits hbm_budget_bytes; admitted requests run concurrently
  * on their own streams. Each request's result equals sf_amplitudes on the same

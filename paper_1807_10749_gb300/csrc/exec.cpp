@@ -55,10 +55,10 @@ struct Layout {
   size_t total_slots = 0;
 };
 
-Layout make_layout(const Plan& p, uint64_t n_finals) {
+Layout make_layout(const Plan& p, uint64_t n_finals, int64_t budget_override = 0) {
   const int nL = (int)p.levels.size();
   const size_t nb = node_bytes(p);
-  int64_t budget = p.opts.hbm_budget_bytes;
+  int64_t budget = budget_override > 0 ? budget_override : p.opts.hbm_budget_bytes;
   const size_t amps = ((size_t)1 << p.A.m) + ((size_t)1 << p.B.m);
   int64_t B = p.opts.batch_paths > 0 ? p.opts.batch_paths : std::max<int64_t>(1, ((int64_t)1 << 26) / (int64_t)amps);
   B = std::min<int64_t>(B, std::max<uint64_t>(1, n_finals));
@@ -97,13 +97,13 @@ uint64_t count_finals(const Plan& p, const std::vector<Range>& rs) {
   return n;
 }
 
-void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan) {
+void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan, int* err) {
   static_assert(sizeof(PassLaunch) <= 32764, "kernel parameter block too large");
   if (pp.stages.size() > (size_t)MAX_STAGES || pp.ops.size() > (size_t)MAX_OPS ||
       pp.phases.size() > (size_t)MAX_PHASE_GROUPS || pp.mats.size() > (size_t)2 * MAX_MATS)
     fail(SF_EUNSUPPORTED, "internal: pass program too large");
   L.pass = pp.dev;
-  L.err = plan.d_err;
+  L.err = err;
   std::copy(pp.stages.begin(), pp.stages.end(), L.stages);
   std::copy(pp.ops.begin(), pp.ops.end(), L.ops);
   std::copy(pp.phases.begin(), pp.phases.end(), L.phases);
@@ -154,7 +154,7 @@ double pass_bytes(const DevPass& d, int nodes) {
 
 // Run a segment program for a batch of nodes of one half.
 void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<Job>& jobs,
-                 cudaStream_t st, bool prof) {
+                 cudaStream_t st, bool prof, int* err) {
   if (jobs.empty()) return;
   for (size_t p = 0; p < seg.passes.size(); p++) {
     const PassPlan& pp = seg.passes[p];
@@ -164,7 +164,7 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
       std::memset(scratch.get(), 0, sizeof(PassLaunch));
     }
     PassLaunch* L = scratch.get();
-    fill_launch(*L, pp, plan);
+    fill_launch(*L, pp, plan, err);
     const int tiles = 1 << pp.dev.n_free;
     for (size_t j0 = 0; j0 < jobs.size(); j0 += MAX_NODES) {
       size_t j1 = std::min(jobs.size(), j0 + MAX_NODES);
@@ -184,11 +184,11 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
 
 }  // namespace
 
-size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s) {
+size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget) {
   (void)n;
   double fa;
   auto rs = select_ranges(p, s, &fa);
-  Layout lay = make_layout(p, count_finals(p, rs));
+  Layout lay = make_layout(p, count_finals(p, rs), budget);
   return lay.total_slots * node_bytes(p) + 256;
 }
 
@@ -247,6 +247,10 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   void** cache_slot = (ctx && ctx->cache_slot) ? ctx->cache_slot : &plan.cache;
   const bool prof = ctx ? ctx->profile : true;
   const volatile int* cancel = ctx ? ctx->cancel : nullptr;
+  int* err = (ctx && ctx->err) ? ctx->err : plan.d_err;
+  const uint32_t* tabA = (ctx && ctx->tabA) ? ctx->tabA : plan.d_tabA;
+  const uint32_t* tabB = (ctx && ctx->tabB) ? ctx->tabB : plan.d_tabB;
+  const int64_t budget = ctx ? ctx->budget : 0;
   double fa = 0;
   std::vector<Range> rs = select_ranges(plan, sel, &fa);
   if (n < 0) fail(SF_EINVAL, "negative bitstring count");
@@ -258,7 +262,7 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   }
   if (n == 0 || rs.empty()) return;
   const uint64_t nfin = count_finals(plan, rs);
-  Layout lay = make_layout(plan, nfin);
+  Layout lay = make_layout(plan, nfin, budget);
   const size_t nb = node_bytes(plan);
   const size_t need = lay.total_slots * nb + 256;
   if (!ws || ws_bytes < need)
@@ -294,8 +298,8 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   // gather template
   GatherLaunch G;
   std::memset(&G, 0, sizeof(G));
-  G.tabA = plan.d_tabA;
-  G.tabB = plan.d_tabB;
+  G.tabA = tabA;
+  G.tabB = tabB;
   G.bits = d_bits;
   G.acc = d_out;
   G.n = n;
@@ -443,8 +447,8 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
           }
           computed.push_back(freep);
         }
-        run_segment(*C, plan, plan.A.seg[s], jobsA, st, prof);
-        run_segment(*C, plan, plan.B.seg[s], jobsB, st, prof);
+        run_segment(*C, plan, plan.A.seg[s], jobsA, st, prof, err);
+        run_segment(*C, plan, plan.B.seg[s], jobsB, st, prof, err);
         for (size_t q : computed) slots[q].valid = true;
         prev_ids = ids;
         prev_slot = where;
@@ -485,8 +489,8 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         std::memcpy(g.leafmask, block[i].mask, sizeof(g.leafmask));
         gf.push_back(g);
       }
-      run_segment(*C, plan, finA, jobsA, st, prof);
-      run_segment(*C, plan, finB, jobsB, st, prof);
+      run_segment(*C, plan, finA, jobsA, st, prof, err);
+      run_segment(*C, plan, finB, jobsB, st, prof, err);
       for (size_t g0 = 0; g0 < gf.size(); g0 += GATHER_FINALS) {
         size_t g1 = std::min(gf.size(), g0 + GATHER_FINALS);
         G.n_finals = (int)(g1 - g0);

@@ -305,8 +305,13 @@ struct ExecCtx {
   void** cache_slot = nullptr;
   bool profile = true;
   const volatile int* cancel = nullptr;
+  // device tables, error flag and memory budget to use instead of the plan's
+  const uint32_t* tabA = nullptr;
+  const uint32_t* tabB = nullptr;
+  int* err = nullptr;
+  int64_t budget = 0;
 };
-size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s);
+size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget = 0);
 void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, double* d_out,
               int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
               ExecCtx* ctx = nullptr);

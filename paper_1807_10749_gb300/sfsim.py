@@ -27,7 +27,7 @@ EXPORTED = [
     "sf_selection_size", "sf_selection_ids", "sf_amplitudes", "sf_workspace_size",
     "sf_amplitudes_device", "sf_server_create", "sf_server_submit", "sf_server_wait",
     "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_plan_profile",
-    "sf_plan_profile_read", "sf_last_error",
+    "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_last_error",
 ]
 
 
@@ -91,6 +91,7 @@ def lib():
             "sf_server_destroy": (None, [P]),
             "sf_plan_profile": (i32, [P, i32]),
             "sf_plan_profile_read": (i32, [P, i32, P, P, P]),
+            "sf_amplitudes_device_noalloc": (i32, [P, P, i64, P, P, i32, P]),
             "sf_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -224,6 +225,17 @@ def sf_amplitudes_device(plan, d_bits, sel, d_out, workspace, stream=None, accum
                                       ctypes.c_void_p(d_out.data_ptr()), 1 if accumulate else 0,
                                       ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
                                       ctypes.c_void_p(stream.cuda_stream)))
+
+
+def sf_amplitudes_device_noalloc(plan, d_bits, sel, d_out, stream=None, accumulate=False):
+    """Device form without a workspace argument: its scratch is a fixed array
+    inside the library, so the call allocates no device memory (see sfsim.h)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().sf_amplitudes_device_noalloc(plan, ctypes.c_void_p(d_bits.data_ptr()), d_bits.numel(),
+                                              ctypes.byref(sel), ctypes.c_void_p(d_out.data_ptr()),
+                                              1 if accumulate else 0, ctypes.c_void_p(stream.cuda_stream)))
 
 
 # --------------------------------------------------------------- server
