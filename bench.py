@@ -143,6 +143,24 @@ def cpu_baseline_sample(text, mask, bits_all):
             "seconds": dt}
 
 
+def rank_prefixes(first_ids, world, rank, n_steps):
+    """First path id of each 128-path prefix this rank processes: every
+    world-th prefix of the sorted selection (the ranks' sets are disjoint)."""
+    n_pre = len(first_ids) // 128
+    return [int(first_ids[128 * ((world * s + rank) % n_pre)]) for s in range(n_steps)]
+
+
+def max_over_ranks(value, device=None):
+    """Largest value over all ranks (the job time is the slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores, same metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -225,8 +243,7 @@ def main():
     n_steps_total = args.warmup + args.steps
     # this rank's prefixes: every world-th 128-path subtree of the sorted selection
     first_ids = sfsim.sf_selection_ids(plan.handle, fsel, cap=128 * world * (n_steps_total + 2))
-    n_pre = len(first_ids) // 128
-    prefixes = [int(first_ids[128 * ((world * s + rank) % n_pre)]) for s in range(n_steps_total + 1)]
+    prefixes = rank_prefixes(first_ids, world, rank, n_steps_total + 1)
     sels = [sfsim.selection("range", first=p, count=128) for p in prefixes]
 
     d_bits = torch.from_numpy(bits.view(np.int64)).to(f"cuda:{dev}")
@@ -263,11 +280,7 @@ def main():
     gat_n, gat_s, gat_b = sfsim.sf_plan_profile_read(plan.handle, 1)
     oth_n, _, _ = sfsim.sf_plan_profile_read(plan.handle, 2)
     sfsim.sf_plan_profile(plan.handle, False)
-    t_max = elapsed
-    if world > 1:
-        t = torch.tensor([elapsed], device=f"cuda:{dev}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(elapsed, f"cuda:{dev}")
     paths_total = 128 * args.steps * world
     value = paths_total / t_max
 
@@ -282,11 +295,7 @@ def main():
     t1 = time.perf_counter()
     for i in range(e2e_steps):
         host_out, _ = plan.amplitudes(bits, sels[(args.warmup + i) % len(sels)])
-    e2e_wall = time.perf_counter() - t1
-    if world > 1:
-        t = torch.tensor([e2e_wall], device=f"cuda:{dev}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_wall = float(t.item())
+    e2e_wall = max_over_ranks(time.perf_counter() - t1, f"cuda:{dev}")
     e2e_value = 128 * e2e_steps * world / e2e_wall
 
     if rank == 0:

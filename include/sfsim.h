@@ -124,6 +124,18 @@ SF_API int sf_plan_info(const sf_plan* p, int* n_cross, int* path_bits, int* m_a
  * stages, deferred gates at the last level. */
 SF_API int sf_plan_stats(const sf_plan* p, int* passes_a, int* passes_b, int* stages_a, int* stages_b,
                   int* deferred);
+/* Per-segment breakdown: segment 0 runs from the start to the first branch
+ * level, segment s >= 1 from level s to the next; segment n_levels + 1 is
+ * the last segment with its level folded into the gather (when it is).
+ * half: 0 = A, 1 = B. passes/stages of that segment's program and its
+ * algorithmic bytes for one node (live amplitudes read + written, 8 B). */
+SF_API int sf_plan_segment_stats(const sf_plan* p, int half, int segment, int* passes, int* stages,
+                                 double* bytes_per_node);
+/* Human-readable description of the plan (cut, levels, and per segment and
+ * half the passes: active bits, pins, register stages and their gates), in
+ * the spirit of the per-run logs of the paper's appendices. Writes at most
+ * cap bytes (NUL-terminated) and the full length to *len. */
+SF_API int sf_plan_describe(const sf_plan* p, char* buf, size_t cap, size_t* len);
 SF_API void sf_plan_destroy(sf_plan* p);
 
 /* Path selection (Eq. 3; Section 3). Path ids number the branch choices, the

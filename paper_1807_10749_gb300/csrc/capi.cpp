@@ -2,6 +2,7 @@
 // internal failures into a status code and a thread-local message.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -193,6 +194,38 @@ int sf_plan_stats(const sf_plan* h, int* passes_a, int* passes_b, int* stages_a,
 }
 
 
+
+int sf_plan_segment_stats(const sf_plan* h, int half, int segment, int* passes, int* stages,
+                          double* bytes_per_node) {
+  SF_GUARD_BEGIN
+  if (!h || half < 0 || half > 1) sf::fail(SF_EINVAL, "bad plan or half");
+  const sf::Plan& p = *h->p;
+  const sf::HalfPlan& H = half ? p.B : p.A;
+  const int nL = (int)p.levels.size();
+  const sf::SegmentPlan* seg = nullptr;
+  if (segment >= 0 && segment <= nL) seg = &H.seg[segment];
+  else if (segment == nL + 1 && p.deferred) seg = &H.last_deferred;
+  else sf::fail(SF_EINVAL, "segment out of range");
+  if (passes) *passes = (int)seg->passes.size();
+  if (stages) *stages = seg->n_stages;
+  if (bytes_per_node) *bytes_per_node = sf::segment_bytes(*seg);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_plan_describe(const sf_plan* h, char* buf, size_t cap, size_t* len) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  std::string t = sf::plan_describe(*h->p);
+  if (len) *len = t.size();
+  if (buf && cap) {
+    size_t n = std::min(cap - 1, t.size());
+    std::memcpy(buf, t.data(), n);
+    buf[n] = 0;
+  }
+  return SF_OK;
+  SF_GUARD_END
+}
 
 static void free_host_buffers(HostBuffers& hb) {
   if (hb.ws) cudaFree(hb.ws);

@@ -184,6 +184,12 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
 
 }  // namespace
 
+double segment_bytes(const SegmentPlan& s) {
+  double b = 0;
+  for (auto& pp : s.passes) b += pass_bytes(pp.dev, 1);
+  return b;
+}
+
 size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget) {
   (void)n;
   double fa;

@@ -172,60 +172,28 @@ __device__ __forceinline__ void dispatch_g2(int a, int b, float2* v, const float
 #undef SF_C2
 }
 
-// Phase group on a register block. gfix: global index of the thread's fixed
-// bits; gr[j]: global position of register bit j. k(i) is a quadratic form in
-// the register bits, evaluated in Gray-code order (one update per amplitude).
+// Phase group on a register block: the quadratic form of DevPhaseGroup,
+// evaluated in Gray-code order (one update per amplitude), then a multiply by
+// e^{i pi k/4} from a table in shared memory.
 template <int R>
 __device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* v, uint32_t gfix,
-                                            const int* gr, const uint8_t* xshift, const uint8_t* xbits,
-                                            uint64_t path, const float2* w8) {
+                                            const uint8_t* xshift, const uint8_t* xbits, uint64_t path,
+                                            const float2* w8) {
   int k0 = __popc(gfix & g.m1) + 2 * __popc(gfix & g.m2) + 4 * __popc(gfix & g.m4);
+  for (int c = 0; c < g.nsh; c++) k0 += 4 * __popc(gfix & (gfix >> g.sh[c]) & g.shm[c]);
   int w[R];
-  uint32_t q[R];
-  uint32_t rmask = 0;
 #pragma unroll
-  for (int j = 0; j < R; j++) {
-    const int p = gr[j];
-    w[j] = (int)((g.m1 >> p) & 1u) + 2 * (int)((g.m2 >> p) & 1u) + 4 * (int)((g.m4 >> p) & 1u);
-    q[j] = 0;
-    rmask |= 1u << p;
-  }
-  for (int c = 0; c < g.ncz; c++) {
-    const int p0 = g.cz[c][0], p1 = g.cz[c][1];
-    const bool r0 = (rmask >> p0) & 1u, r1 = (rmask >> p1) & 1u;
-    if (!r0 && !r1) {
-      k0 += 4 * (int)((gfix >> p0) & (gfix >> p1) & 1u);
-    } else {
-#pragma unroll
-      for (int j = 0; j < R; j++) {
-        if (r0 && r1) {
-          if (gr[j] == p0) {
-#pragma unroll
-            for (int l = 0; l < R; l++)
-              if (gr[l] == p1) q[j] |= 1u << l;
-          } else if (gr[j] == p1) {
-#pragma unroll
-            for (int l = 0; l < R; l++)
-              if (gr[l] == p0) q[j] |= 1u << l;
-          }
-        } else if (r0 && gr[j] == p0) {
-          w[j] += 4 * (int)((gfix >> p1) & 1u);
-        } else if (r1 && gr[j] == p1) {
-          w[j] += 4 * (int)((gfix >> p0) & 1u);
-        }
-      }
-    }
-  }
+  for (int j = 0; j < R; j++) w[j] = (int)g.wstat[j] + 4 * __popc(gfix & g.czf[j]);
   for (int s = 0; s < g.nsel; s++) {
-    const int p = g.sel[s].pos;
     const int d = g.sel[s].xi >= 0 ? digit_of(xshift, xbits, path, g.sel[s].xi) : 0;
     const int ws = g.sel[s].w[d];
-    if ((rmask >> p) & 1u) {
+    const int r = g.sel[s].reg;
+    if (r >= 0) {
 #pragma unroll
       for (int j = 0; j < R; j++)
-        if (gr[j] == p) w[j] += ws;
+        if (j == r) w[j] += ws;
     } else {
-      k0 += ws * (int)((gfix >> p) & 1u);
+      k0 += ws * (int)((gfix >> g.sel[s].pos) & 1u);
     }
   }
   int kk = k0;
@@ -236,7 +204,7 @@ __device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* v, u
     const int prev = (i - 1) ^ ((i - 1) >> 1);
     const int j = cctz(gi ^ prev);  // flipped bit (compile time)
     const int rest = gi & ~(1 << j);
-    const int delta = w[j] + 4 * __popc(q[j] & (uint32_t)rest);
+    const int delta = w[j] + 4 * __popc((uint32_t)g.czq[j] & (uint32_t)rest);
     if (gi & (1 << j)) kk += delta;
     else kk -= delta;
     v[gi] = cmul(v[gi], w8[kk & 7]);
@@ -354,9 +322,25 @@ __device__ __forceinline__ void issue_loads(const PassLaunch& P, const ItemGeo& 
   }
 }
 
-template <int R>
+__device__ __forceinline__ void compute_bar(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+__device__ __forceinline__ bool compute_bar_or(int nthreads, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int R, bool GEN>
 __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
-                                           float post_scale) {
+                                           float post_scale, int ncomp) {
   const DevPass& d = P.pass;
   const int k = d.k;
   for (int s = 0; s < d.n_stages; s++) {
@@ -369,18 +353,13 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
       gr[j] = d.gpos[st.rbit[j]];
       rl |= 1u << st.rbit[j];
     }
-    uint32_t lfix = 0;
-    {
-      uint32_t t = threadIdx.x;
-      for (int j = 0; j < k; j++) {
-        if ((rl >> j) & 1u) continue;
-        lfix |= (t & 1u) << j;
-        t >>= 1;
-      }
+    uint32_t lfix = 0, gfix = g.base;
+    for (int t = 0; t < k - R; t++) {
+      const uint32_t b = (threadIdx.x >> t) & 1u;
+      lfix |= b << st.tpos[t];
+      gfix |= b << st.tg[t];
     }
-    uint32_t gfix = g.base;
-    for (int j = 0; j < k; j++)
-      if ((lfix >> j) & 1u) gfix |= 1u << d.gpos[j];
+    (void)rl;
     float2 v[1 << R];
     {
       int addr = (int)lfix;
@@ -401,42 +380,48 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
         case DOP_YH:
           dispatch_1q<R>(op.code, op.a, v);
           break;
-        case DOP_G1: {
-          const float* m = P.mats + 2 * op.arg;
-          dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
-                         make_float2(m[4], m[5]), make_float2(m[6], m[7]));
-          break;
-        }
-        case DOP_G1SEL: {
-          const int dg = digit_of(P.xshift, P.xbits, g.path, op.xi);
-          const float* m = P.mats + 2 * (op.arg + 4 * dg);
-          dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
-                         make_float2(m[4], m[5]), make_float2(m[6], m[7]));
-          break;
-        }
-        case DOP_G2:
-          dispatch_g2<R>(op.a, op.b, v, P.mats + 2 * op.arg);
-          break;
         case DOP_PHASE:
-          apply_phase<R>(P.phases[op.arg], v, gfix, gr, P.xshift, P.xbits, g.path, w8);
+          apply_phase<R>(P.phases[op.arg], v, gfix, P.xshift, P.xbits, g.path, w8);
           break;
-        case DOP_DMUL: {
-          const float* m = P.mats + 2 * op.arg;
-          const float2 f0 = make_float2(m[0], m[1]), f1 = make_float2(m[2], m[3]);
-          int jr = -1;
-#pragma unroll
-          for (int j = 0; j < R; j++)
-            if (gr[j] == op.a) jr = j;
-          if (jr >= 0) {
-            dispatch_dmul<R>(jr, v, f0, f1);
-          } else {
-            const float2 f = ((gfix >> op.a) & 1u) ? f1 : f0;
-#pragma unroll
-            for (int i = 0; i < (1 << R); i++) v[i] = cmul(f, v[i]);
-          }
-          break;
-        }
         default:
+          if constexpr (GEN) {
+            switch (op.code) {
+            case DOP_G1: {
+              const float* m = P.mats + 2 * op.arg;
+              dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                             make_float2(m[4], m[5]), make_float2(m[6], m[7]));
+              break;
+            }
+            case DOP_G1SEL: {
+              const int dg = digit_of(P.xshift, P.xbits, g.path, op.xi);
+              const float* m = P.mats + 2 * (op.arg + 4 * dg);
+              dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                             make_float2(m[4], m[5]), make_float2(m[6], m[7]));
+              break;
+            }
+            case DOP_G2:
+              dispatch_g2<R>(op.a, op.b, v, P.mats + 2 * op.arg);
+              break;
+            case DOP_DMUL: {
+              const float* m = P.mats + 2 * op.arg;
+              const float2 f0 = make_float2(m[0], m[1]), f1 = make_float2(m[2], m[3]);
+              int jr = -1;
+#pragma unroll
+              for (int j = 0; j < R; j++)
+                if (gr[j] == op.a) jr = j;
+              if (jr >= 0) {
+                dispatch_dmul<R>(jr, v, f0, f1);
+              } else {
+                const float2 f = ((gfix >> op.a) & 1u) ? f1 : f0;
+#pragma unroll
+                for (int i = 0; i < (1 << R); i++) v[i] = cmul(f, v[i]);
+              }
+              break;
+            }
+            default:
+                break;
+            }
+          }
           break;
       }
     }
@@ -452,26 +437,36 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
         sm[addr] = make_float2(v[gi].x * sc, v[gi].y * sc);
       }
     }
-    __syncthreads();
+    compute_bar(ncomp);
   }
 }
 
-// Persistent fused pass. Each CTA walks work items (node, tile) with stride
-// gridDim.x; tiles move between global and shared memory as runs of 2^L
-// contiguous amplitudes with TMA bulk copies, double-buffered: the loads of
-// item i+2 run while item i+1 is computed. Input-pinned (structurally zero)
-// runs are never read and output-pinned runs never written.
-template <int R>
-__global__ void __launch_bounds__(256, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
-  constexpr int NBUF = 2;
+// Persistent fused pass, warp-specialised. Each CTA walks work items
+// (node, tile) with stride gridDim.x through NBUF shared-memory tile buffers.
+// The last warp is the producer: it moves tiles between global and shared
+// memory as runs of 2^L contiguous amplitudes with TMA bulk copies (loads
+// complete on full[b]; a buffer's outgoing stores are issued once the compute
+// warps arrive on empty[b]). The compute warps run the register stages and
+// synchronise only among themselves (named barrier 1), so copies and gates
+// overlap. Input-pinned (structurally zero) runs are never read and
+// output-pinned runs never written. Every wait is bounded; a timeout sets the
+// error flag and ends the kernel.
+template <int R, bool GEN>
+__global__ void __launch_bounds__(288, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
+  constexpr int NBUF = 3;
   extern __shared__ __align__(128) unsigned char smem[];
   const DevPass& d = P.pass;
   const int k = d.k, L = d.L;
   const int ntile = 1 << k, nruns = 1 << (k - L);
+  const int nact = 1 << (k - R);                 // compute threads doing stage work
+  const int ncw = (nact + 31) >> 5;               // compute warps
+  const int ncomp = ncw * 32;
   float2* bufs = reinterpret_cast<float2*>(smem);
   uint32_t* runoff = reinterpret_cast<uint32_t*>(bufs + NBUF * ntile);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(runoff + ((nruns + 1) & ~1));
+  uint64_t* full = reinterpret_cast<uint64_t*>(runoff + ((nruns + 1) & ~1));
+  uint64_t* empty = full + NBUF;
   __shared__ float2 w8[8];
+  __shared__ int abort_flag;
   const int tiles_log2 = d.n_free;
   const int64_t items = (int64_t)P.n_nodes << tiles_log2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -479,8 +474,12 @@ __global__ void __launch_bounds__(256, 1) pass_kernel(const __grid_constant__ Pa
 
   if (threadIdx.x < 8) {
     const float r = 0.70710678118654752f;
-    const float2 t8[8] = {{1.f, 0.f}, {r, r}, {0.f, 1.f}, {-r, r}, {-1.f, 0.f}, {-r, -r}, {0.f, -1.f}, {r, -r}};
-    w8[threadIdx.x] = t8[threadIdx.x];
+    const float c = (threadIdx.x & 1) ? r : 1.0f;
+    // e^{i pi t/4}: (cos, sin) from the octant
+    const int t = threadIdx.x;
+    float re = (t == 0) ? 1.f : (t == 2 || t == 6) ? 0.f : (t == 4) ? -1.f : (t == 1 || t == 7) ? c : -c;
+    float im = (t == 2) ? 1.f : (t == 6) ? -1.f : (t == 0 || t == 4) ? 0.f : (t == 1 || t == 3) ? c : -c;
+    w8[t] = make_float2(re, im);
   }
   for (int rI = threadIdx.x; rI < nruns; rI += blockDim.x) {
     uint32_t hi = 0;
@@ -488,68 +487,92 @@ __global__ void __launch_bounds__(256, 1) pass_kernel(const __grid_constant__ Pa
     runoff[rI] = hi;
   }
   if (threadIdx.x == 0) {
-    for (int b = 0; b < NBUF; b++) mbar_init(smem_u32(&bars[b]), 1);
+    abort_flag = 0;
+    for (int b = 0; b < NBUF; b++) {
+      mbar_init(smem_u32(&full[b]), 1);
+      mbar_init(smem_u32(&empty[b]), ncw);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int b = 0; b < NBUF; b++) {
-      const int64_t it = blockIdx.x + (int64_t)b * gridDim.x;
-      if (it < items) issue_loads(P, item_geo(P, it, tiles_log2), runoff, smem_u32(bufs + b * ntile),
-                                  smem_u32(&bars[b]), lane);
+
+  if (warp == ncw) {
+    // ------------------------------------------------------------ producer
+    int i = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < items + (int64_t)NBUF * gridDim.x && ok; it += gridDim.x, i++) {
+      const int b = i % NBUF;
+      const uint32_t src = smem_u32(bufs + b * ntile);
+      if (i >= NBUF) {
+        // the item that used buffer b before: wait until computed, store it
+        const int64_t prev = it - (int64_t)NBUF * gridDim.x;
+        if (prev < items) {
+          if (!mbar_wait(smem_u32(&empty[b]), (uint32_t)((i / NBUF - 1) & 1)) || *(volatile int*)&abort_flag) {
+            ok = false;
+            break;
+          }
+          const ItemGeo g = item_geo(P, prev, tiles_log2);
+          float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
+          const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
+          for (int r = lane; r < nruns; r += 32) {
+            if (((uint32_t)r & rm) != rv) continue;
+            bulk_s2g(out + (g.base | runoff[r]), src + (uint32_t)r * run_bytes, run_bytes);
+          }
+          bulk_commit();
+          bulk_wait_read0();
+          __syncwarp();
+        }
+      }
+      if (it < items) {
+        fence_async_smem();
+        issue_loads(P, item_geo(P, it, tiles_log2), runoff, src, smem_u32(&full[b]), lane);
+      }
     }
+    if (!ok && lane == 0) {
+      abort_flag = 1;
+      atomicExch(P.err, 1);
+    }
+    bulk_wait0();
+    return;
   }
+
+  // -------------------------------------------------------------- compute
   int i = 0;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
     const int b = i % NBUF;
-    const uint32_t parity = (uint32_t)((i / NBUF) & 1);
     float2* sm = bufs + b * ntile;
     const ItemGeo g = item_geo(P, it, tiles_log2);
-    const int timed_out = mbar_wait(smem_u32(&bars[b]), parity) ? 0 : 1;
-    if (__syncthreads_or(timed_out)) {
-      if (threadIdx.x == 0) atomicExch(P.err, 1);
+    const bool timed_out = !mbar_wait(smem_u32(&full[b]), (uint32_t)((i / NBUF) & 1));
+    if (compute_bar_or(ncomp, timed_out || *(volatile int*)&abort_flag)) {
+      if (threadIdx.x == 0) {
+        abort_flag = 1;
+        atomicExch(P.err, 1);
+      }
       break;
     }
-    // generated input, or zeros at input-pinned positions
     if (d.gen_input) {
-      for (int e = threadIdx.x; e < ntile; e += blockDim.x)
+      for (int e = threadIdx.x; e < ntile; e += ncomp)
         sm[e] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-      __syncthreads();
+      compute_bar(ncomp);
     } else if (g.lin_m) {
-      for (int e = threadIdx.x; e < ntile; e += blockDim.x)
+      for (int e = threadIdx.x; e < ntile; e += ncomp)
         if (((uint32_t)e & g.lin_m) != g.lin_v) sm[e] = make_float2(0.f, 0.f);
-      __syncthreads();
+      compute_bar(ncomp);
     }
-    run_stages<R>(P, sm, g, w8, d.post_scale);
+    if (threadIdx.x < nact) run_stages<R, GEN>(P, sm, g, w8, d.post_scale, ncomp);
+    else
+      for (int s = 0; s < d.n_stages; s++) compute_bar(ncomp);
     if (d.n_stages == 0 && d.post_scale != 1.0f) {
-      for (int e = threadIdx.x; e < ntile; e += blockDim.x) {
+      for (int e = threadIdx.x; e < ntile; e += ncomp) {
         float2 v = sm[e];
         sm[e] = make_float2(v.x * d.post_scale, v.y * d.post_scale);
       }
-      __syncthreads();
     }
-    // shared -> global: the generic-proxy writes must be visible to the TMA
+    // hand the buffer to the producer: generic writes -> async proxy
     fence_async_smem();
-    __syncthreads();
-    if (warp == 0) {
-      float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
-      const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
-      const uint32_t src = smem_u32(sm);
-      for (int r = lane; r < nruns; r += 32) {
-        if (((uint32_t)r & rm) != rv) continue;
-        bulk_s2g(out + (g.base | runoff[r]), src + (uint32_t)r * run_bytes, run_bytes);
-      }
-      bulk_commit();
-      const int64_t nx = it + (int64_t)NBUF * gridDim.x;
-      if (nx < items) {
-        bulk_wait_read0();  // the stores have read this buffer
-        __syncwarp();
-        fence_async_smem();
-        issue_loads(P, item_geo(P, nx, tiles_log2), runoff, src, smem_u32(&bars[b]), lane);
-      }
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&empty[b]));
   }
-  if (warp == 0) bulk_wait0();
 }
 
 // ------------------------------------------------------------------ gather
@@ -698,11 +721,12 @@ static int num_sms() {
   return n;
 }
 
-template <int R>
+template <int R, bool GEN>
 static void launch_pass_r(const PassLaunch& L, int tiles, int tile_k, cudaStream_t s) {
-  const int threads = 1 << (tile_k - R);
+  const int nact = 1 << (tile_k - R);
+  const int threads = ((nact + 31) / 32) * 32 + 32;  // compute warps + the producer warp
   const int nruns = 1 << (tile_k - L.pass.L);
-  const size_t smem = 2 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 2 * 8;
+  const size_t smem = 3 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 6 * 8;
   // The dynamic shared-memory limit is a property of the kernel function, so
   // it only ever grows; occupancy is cached per tile size.
   static std::mutex mu;
@@ -712,13 +736,13 @@ static void launch_pass_r(const PassLaunch& L, int tiles, int tile_k, cudaStream
   {
     std::lock_guard<std::mutex> lk(mu);
     if (smem > smem_set) {
-      check(cudaFuncSetAttribute(pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+      check(cudaFuncSetAttribute(pass_kernel<R, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
             "cudaFuncSetAttribute");
       smem_set = smem;
     }
     if (!per_sm[tile_k]) {
       int v = 0;
-      check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, pass_kernel<R>, threads, smem),
+      check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, pass_kernel<R, GEN>, threads, smem),
             "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
       per_sm[tile_k] = v > 0 ? v : 1;
     }
@@ -727,7 +751,7 @@ static void launch_pass_r(const PassLaunch& L, int tiles, int tile_k, cudaStream
   const int64_t items = (int64_t)tiles * L.n_nodes;
   int64_t grid = std::min<int64_t>(items, (int64_t)num_sms() * nb);
   if (grid < 1) return;
-  pass_kernel<R><<<(int)grid, threads, smem, s>>>(L);
+  pass_kernel<R, GEN><<<(int)grid, threads, smem, s>>>(L);
   check(cudaGetLastError(), "pass_kernel launch");
 }
 
@@ -738,14 +762,22 @@ void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, v
   if (k - R > 8 || k > 13 || R < 1) fail(SF_EINVAL, "internal: bad tile shape");
   (void)fuse_bits;
   (void)tile_bits;
+  bool gen = false;  // does the pass need the general-gate variant?
+  for (int i = 0; i < L.pass.n_stages; i++)
+    for (int o = L.stages[i].op_begin; o < L.stages[i].op_end; o++) {
+      const int c = L.ops[o].code;
+      if (c == DOP_G1 || c == DOP_G1SEL || c == DOP_G2 || c == DOP_DMUL || c == DOP_DMULSEL) gen = true;
+    }
+#define SF_R(RR)                                                   \
+  case RR:                                                         \
+    if (gen) launch_pass_r<RR, true>(L, tiles, k, s);              \
+    else launch_pass_r<RR, false>(L, tiles, k, s);                 \
+    break;
   switch (R) {
-    case 1: launch_pass_r<1>(L, tiles, k, s); break;
-    case 2: launch_pass_r<2>(L, tiles, k, s); break;
-    case 3: launch_pass_r<3>(L, tiles, k, s); break;
-    case 4: launch_pass_r<4>(L, tiles, k, s); break;
-    case 5: launch_pass_r<5>(L, tiles, k, s); break;
+    SF_R(1) SF_R(2) SF_R(3) SF_R(4) SF_R(5)
     default: fail(SF_EINVAL, "internal: bad register bits");
   }
+#undef SF_R
 }
 
 void launch_gather(const GatherLaunch& L, void* stream) {

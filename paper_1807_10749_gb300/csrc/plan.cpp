@@ -14,6 +14,7 @@
 //                             slices)
 #include <algorithm>
 #include <array>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -190,11 +191,13 @@ HOp local_op(const Gate& g, int p0, int p1, cd& global) {
     }
     return o;
   }
-  if (g.kind == SF_H) { o.kind = H_G1; o.fast = DOP_H; o.scale_e = 1; }
-  else if (g.kind == SF_X_HALF) { o.kind = H_G1; o.fast = DOP_XH; o.scale_e = 2; }
-  else if (g.kind == SF_Y_HALF) { o.kind = H_G1; o.fast = DOP_YH; o.scale_e = 2; }
   for (int i = 0; i < 4; i++) o.m[i] = m[i];
-  if (o.kind == H_G1) return o;
+  if (g.kind == SF_H || g.kind == SF_X_HALF || g.kind == SF_Y_HALF) {
+    o.kind = H_G1;
+    o.fast = g.kind == SF_H ? DOP_H : (g.kind == SF_X_HALF ? DOP_XH : DOP_YH);
+    o.scale_e = g.kind == SF_H ? 1 : 2;
+    return o;
+  }
   bool diag = near(m[1], 0, 0) && near(m[2], 0, 0);
   if (diag) {
     // diag(a, b) = a * diag(1, b/a); a power of e^{i pi/4} ratio -> mod-8 phase
@@ -237,8 +240,130 @@ struct Emitter {
   }
 };
 
-bool emit_stage_ops(const std::vector<const HOp*>& ops, const DevStage& st, const int* local_of,
-                    PassPlan& pp) {
+// Collected diagonal gates of one phase group before it is laid out for
+// its stage.
+struct GroupAcc {
+  int w[32] = {0};
+  std::vector<std::pair<int, int>> cz;  // (a < b), repeated pairs cancel
+  struct Sel {
+    int pos, xi;
+    int w[4];
+  };
+  std::vector<Sel> sel;
+};
+
+// Lay a collected group out for a stage whose register bit j sits at global
+// position gr[j]. Returns false if it needs more shift classes than fit.
+bool finish_group(const GroupAcc& acc, const int* gr, int R, DevPhaseGroup& g) {
+  std::memset(&g, 0, sizeof(g));
+  uint32_t rmask = 0;
+  for (int j = 0; j < R; j++) rmask |= 1u << gr[j];
+  for (int p = 0; p < 32; p++) {
+    int w = ((acc.w[p] % 8) + 8) % 8;
+    if ((rmask >> p) & 1u) {
+      for (int j = 0; j < R; j++)
+        if (gr[j] == p) g.wstat[j] = (uint8_t)w;
+      continue;
+    }
+    if (w & 1) g.m1 |= 1u << p;
+    if (w & 2) g.m2 |= 1u << p;
+    if (w & 4) g.m4 |= 1u << p;
+  }
+  auto reg = [&](int p) {
+    for (int j = 0; j < R; j++)
+      if (gr[j] == p) return j;
+    return -1;
+  };
+  for (auto& pr : acc.cz) {
+    const int a = pr.first, b = pr.second;
+    const int ja = reg(a), jb = reg(b);
+    if (ja >= 0 && jb >= 0) {
+      g.czq[ja] |= (uint8_t)(1u << jb);
+      g.czq[jb] |= (uint8_t)(1u << ja);
+    } else if (ja >= 0) {
+      g.czf[ja] |= 1u << b;
+    } else if (jb >= 0) {
+      g.czf[jb] |= 1u << a;
+    } else {
+      const int sh = b - a;
+      int c = 0;
+      while (c < g.nsh && g.sh[c] != sh) c++;
+      if (c == g.nsh) {
+        if (g.nsh >= MAX_SHIFTS) return false;
+        g.sh[g.nsh++] = (uint8_t)sh;
+      }
+      g.shm[c] |= 1u << a;
+    }
+  }
+  if ((int)acc.sel.size() > MAX_SEL_PER_GROUP) return false;
+  g.nsel = (int)acc.sel.size();
+  for (size_t i = 0; i < acc.sel.size(); i++) {
+    g.sel[i].pos = (int8_t)acc.sel[i].pos;
+    g.sel[i].xi = (int8_t)acc.sel[i].xi;
+    g.sel[i].reg = (int8_t)reg(acc.sel[i].pos);
+    for (int d = 0; d < 4; d++) g.sel[i].w[d] = (uint8_t)acc.sel[i].w[d];
+  }
+  return true;
+}
+
+// Order a stage's ops with as few phase groups as possible. Diagonal ops
+// commute with each other and with every op on other qubits, so each may sit
+// anywhere between the last earlier and the first later non-diagonal op that
+// shares a qubit with it; a greedy point cover of those intervals (by right
+// end) picks the fewest slots, and all diagonal ops of a slot form one group.
+std::vector<const HOp*> merge_diagonals(const std::vector<const HOp*>& ops) {
+  std::vector<const HOp*> nd;
+  std::vector<int> nd_idx;
+  for (size_t i = 0; i < ops.size(); i++)
+    if (!ops[i]->diag()) {
+      nd.push_back(ops[i]);
+      nd_idx.push_back((int)i);
+    }
+  const int N = (int)nd.size();
+  struct Iv {
+    int lo, hi;
+    const HOp* op;
+  };
+  std::vector<Iv> iv;
+  for (size_t i = 0; i < ops.size(); i++) {
+    if (!ops[i]->diag()) continue;
+    const uint64_t b = op_posmask(*ops[i]);
+    int lo = 0, hi = N;
+    for (int j = 0; j < N; j++) {
+      if (!(op_posmask(*nd[j]) & b)) continue;
+      if (nd_idx[j] < (int)i) lo = j + 1;
+      else {
+        hi = j;
+        break;
+      }
+    }
+    iv.push_back({lo, hi, ops[i]});
+  }
+  std::vector<int> slot_of(iv.size(), -1);
+  std::vector<size_t> order(iv.size());
+  for (size_t i = 0; i < order.size(); i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return iv[a].hi < iv[b].hi; });
+  int chosen = -1;
+  for (size_t t : order) {
+    if (chosen >= iv[t].lo && chosen <= iv[t].hi) {
+      slot_of[t] = chosen;
+      continue;
+    }
+    chosen = iv[t].hi;
+    slot_of[t] = chosen;
+  }
+  std::vector<const HOp*> out;
+  for (int sl = 0; sl <= N; sl++) {
+    for (size_t t = 0; t < iv.size(); t++)  // diagonal ops of this slot, original order
+      if (slot_of[t] == sl) out.push_back(iv[t].op);
+    if (sl < N) out.push_back(nd[sl]);
+  }
+  return out;
+}
+
+bool emit_stage_ops(const std::vector<const HOp*>& ops_in, const DevStage& st, const int* local_of,
+                    const int8_t* gpos, PassPlan& pp) {
+  const std::vector<const HOp*> ops = merge_diagonals(ops_in);
   Emitter em(pp);
   auto reg_of = [&](int pos) {
     int lb = local_of[pos];
@@ -246,19 +371,15 @@ bool emit_stage_ops(const std::vector<const HOp*>& ops, const DevStage& st, cons
       if (st.rbit[j] == lb) return j;
     return -1;
   };
+  int gr[MAX_R];
+  for (int j = 0; j < st.r; j++) gr[j] = gpos[st.rbit[j]];
   int cur_group = -1;
-  std::vector<int> wsum(32, 0);
+  GroupAcc acc;
+  bool ok = true;
   auto close_group = [&]() {
     if (cur_group < 0) return;
-    DevPhaseGroup& g = pp.phases[cur_group];
-    g.m1 = g.m2 = g.m4 = 0;
-    for (int p = 0; p < 32; p++) {
-      int w = ((wsum[p] % 8) + 8) % 8;
-      if (w & 1) g.m1 |= 1u << p;
-      if (w & 2) g.m2 |= 1u << p;
-      if (w & 4) g.m4 |= 1u << p;
-    }
-    std::fill(wsum.begin(), wsum.end(), 0);
+    if (!finish_group(acc, gr, st.r, pp.phases[cur_group])) ok = false;
+    acc = GroupAcc();
     cur_group = -1;
   };
   auto open_group = [&]() {
@@ -275,41 +396,23 @@ bool emit_stage_ops(const std::vector<const HOp*>& ops, const DevStage& st, cons
   for (const HOp* o : ops) {
     if (o->kind == H_CZ || o->kind == H_PHASE1 || o->kind == H_XPHASE) {
       if (!open_group()) return false;
-      DevPhaseGroup& g = pp.phases[cur_group];
       if (o->kind == H_PHASE1) {
-        wsum[o->p0] += o->w;
+        acc.w[o->p0] += o->w;
       } else if (o->kind == H_CZ) {
-        // a repeated pair cancels (CZ^2 = I)
-        int a = std::min(o->p0, o->p1), b = std::max(o->p0, o->p1);
-        bool found = false;
-        for (int i = 0; i < g.ncz; i++)
-          if (g.cz[i][0] == a && g.cz[i][1] == b) {
-            g.cz[i][0] = g.cz[g.ncz - 1][0];
-            g.cz[i][1] = g.cz[g.ncz - 1][1];
-            g.ncz--;
-            found = true;
-            break;
-          }
-        if (!found) {
-          if (g.ncz >= MAX_CZ_PER_GROUP) {
-            close_group();
-            if (!open_group()) return false;
-          }
-          DevPhaseGroup& g2 = pp.phases[cur_group];
-          g2.cz[g2.ncz][0] = (int8_t)a;
-          g2.cz[g2.ncz][1] = (int8_t)b;
-          g2.ncz++;
-        }
+        const int a = std::min(o->p0, o->p1), b = std::max(o->p0, o->p1);
+        auto it = std::find(acc.cz.begin(), acc.cz.end(), std::make_pair(a, b));
+        if (it != acc.cz.end()) acc.cz.erase(it);  // CZ^2 = I
+        else acc.cz.push_back({a, b});
       } else {
-        if (g.nsel >= MAX_SEL_PER_GROUP) {
+        if ((int)acc.sel.size() >= MAX_SEL_PER_GROUP) {
           close_group();
           if (!open_group()) return false;
         }
-        DevPhaseGroup& g2 = pp.phases[cur_group];
-        auto& s = g2.sel[g2.nsel++];
-        s.pos = (int8_t)o->p0;
-        s.xi = (int8_t)o->xi;
-        for (int d = 0; d < 4; d++) s.w[d] = (uint8_t)(d < o->nterm ? o->tw[d] : 0);
+        GroupAcc::Sel sl;
+        sl.pos = o->p0;
+        sl.xi = o->xi;
+        for (int d = 0; d < 4; d++) sl.w[d] = d < o->nterm ? o->tw[d] : 0;
+        acc.sel.push_back(sl);
       }
       continue;
     }
@@ -351,10 +454,11 @@ bool emit_stage_ops(const std::vector<const HOp*>& ops, const DevStage& st, cons
     }
     if ((d.code == DOP_G1 || d.code == DOP_G1SEL || d.code == DOP_G2 || d.code <= DOP_YH) && d.a < 0)
       fail(SF_EINVAL, "internal: op bit not in register block");
+    if (d.code == DOP_G2 && d.b < 0) fail(SF_EINVAL, "internal: op bit not in register block");
     pp.ops.push_back(d);
   }
   close_group();
-  return (int)pp.mats.size() <= 2 * MAX_MATS && (int)pp.ops.size() <= MAX_OPS;
+  return ok && (int)pp.mats.size() <= 2 * MAX_MATS && (int)pp.ops.size() <= MAX_OPS;
 }
 
 DevPin to_dev(const Pin& p) {
@@ -381,7 +485,7 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
     }
   }
   const int k = std::min(tile_bits, m);
-  const int L = std::min(5, k);
+  const int L = std::min(4, k);
   // register bits: at most the fusion width, at least enough that a tile
   // needs no more than 256 threads, and leave >= 2^min(5,k-1) threads per tile
   int R = std::max(1, std::min(fuse_bits, k - std::min(5, k - 1)));
@@ -391,36 +495,125 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
   bool first = true;
   out.passes.clear();
   out.n_stages = 0;
+  const uint64_t low = (L >= 64) ? ~0ull : ((1ull << L) - 1);
+  // Ops that run in one pass whose active set is S: in order, an op runs if
+  // no earlier op on its bits was held back and its non-diagonal bits are in S.
+  auto take_fixed = [&](const std::vector<const HOp*>& ops, uint64_t S, int cap,
+                        std::vector<const HOp*>* taken, std::vector<const HOp*>* rest) {
+    uint64_t blocked = 0;
+    int n = 0;
+    for (const HOp* o : ops) {
+      const uint64_t b = op_posmask(*o);
+      if (n >= cap || (b & blocked) || (!o->diag() && (b & ~S))) {
+        blocked |= b;
+        if (rest) rest->push_back(o);
+        continue;
+      }
+      n++;
+      if (taken) taken->push_back(o);
+    }
+    return n;
+  };
+  // First-come active set: bits join as the ops that need them are reached.
+  auto greedy_S = [&](const std::vector<const HOp*>& ops) {
+    uint64_t S = low, blocked = 0;
+    for (const HOp* o : ops) {
+      const uint64_t b = op_posmask(*o);
+      if (b & blocked) {
+        blocked |= b;
+        continue;
+      }
+      if (o->diag()) continue;
+      const uint64_t need = b & ~S;
+      if (__builtin_popcountll(S | need) <= k) S |= need;
+      else blocked |= b;
+    }
+    return S;
+  };
+  auto greedy_passes = [&](std::vector<const HOp*> ops) {
+    int n = 0;
+    while (!ops.empty() && n < 64) {
+      std::vector<const HOp*> rest;
+      take_fixed(ops, greedy_S(ops), MAX_OPS, nullptr, &rest);
+      if (rest.size() == ops.size()) return 1000;  // no progress (cannot happen)
+      ops.swap(rest);
+      n++;
+    }
+    return n;
+  };
+  // Active set for the next pass: the first-come set, or one built from an
+  // ordering of the bits the remaining non-diagonal ops need, whichever
+  // leaves the fewest passes for the rest of the segment.
+  auto choose_S = [&](const std::vector<const HOp*>& ops) {
+    std::vector<uint64_t> cands;
+    cands.push_back(greedy_S(ops));
+    std::vector<int> first(m, 1 << 30), last(m, -1), cnt(m, 0);
+    for (size_t i = 0; i < ops.size(); i++) {
+      if (ops[i]->diag()) continue;
+      for (int p : {ops[i]->p0, ops[i]->p1}) {
+        if (p < 0 || ((low >> p) & 1)) continue;
+        first[p] = std::min(first[p], (int)i);
+        last[p] = std::max(last[p], (int)i);
+        cnt[p]++;
+      }
+    }
+    std::vector<int> bits;
+    for (int p = 0; p < m; p++)
+      if (cnt[p]) bits.push_back(p);
+    auto from_order = [&](const std::vector<int>& order) {
+      uint64_t S = low;
+      for (int p : order)
+        if (__builtin_popcountll(S) < k) S |= 1ull << p;
+      return S;
+    };
+    std::vector<int> o = bits;
+    std::sort(o.begin(), o.end(), [&](int a, int b) { return first[a] < first[b]; });
+    cands.push_back(from_order(o));
+    std::sort(o.begin(), o.end(), [&](int a, int b) { return last[a] < last[b]; });
+    cands.push_back(from_order(o));
+    std::sort(o.begin(), o.end(), [&](int a, int b) { return cnt[a] > cnt[b] || (cnt[a] == cnt[b] && first[a] < first[b]); });
+    cands.push_back(from_order(o));
+    std::sort(o.begin(), o.end());
+    cands.push_back(from_order(o));
+    std::reverse(o.begin(), o.end());
+    cands.push_back(from_order(o));
+    uint64_t rng = 0x9E3779B97F4A7C15ull ^ (uint64_t)ops.size();
+    for (int t = 0; t < 24; t++) {
+      std::vector<int> r = bits;
+      for (size_t i = r.size(); i > 1; i--) {
+        rng ^= rng << 13;
+        rng ^= rng >> 7;
+        rng ^= rng << 17;
+        std::swap(r[i - 1], r[rng % i]);
+      }
+      cands.push_back(from_order(r));
+    }
+    uint64_t best = cands[0];
+    int best_passes = 1 << 30, best_taken = -1;
+    for (uint64_t S : cands) {
+      std::vector<const HOp*> rest;
+      const int n = take_fixed(ops, S, MAX_OPS, nullptr, &rest);
+      if (n == 0 && !ops.empty()) continue;
+      const int passes = 1 + greedy_passes(rest);
+      if (passes < best_passes || (passes == best_passes && n > best_taken)) {
+        best = S;
+        best_passes = passes;
+        best_taken = n;
+      }
+    }
+    return best;
+  };
   while (first || !rem.empty()) {
     int cap = MAX_OPS;
     PassPlan pp;
     std::vector<const HOp*> taken, deferred;
+    const uint64_t S_choice = rem.empty() ? low : choose_S(rem);
     while (true) {
       pp = PassPlan();
       taken.clear();
       deferred.clear();
-      uint64_t S = (L >= 64) ? ~0ull : ((1ull << L) - 1);
-      uint64_t blocked = 0;
-      for (const HOp* o : rem) {
-        uint64_t b = op_posmask(*o);
-        if ((int)taken.size() >= cap || (b & blocked)) {
-          blocked |= b;
-          deferred.push_back(o);
-          continue;
-        }
-        if (o->diag()) {
-          taken.push_back(o);
-          continue;
-        }
-        uint64_t need = b & ~S;
-        if (__builtin_popcountll(S | need) <= k) {
-          S |= need;
-          taken.push_back(o);
-        } else {
-          blocked |= b;
-          deferred.push_back(o);
-        }
-      }
+      uint64_t S = S_choice;
+      take_fixed(rem, S, cap, &taken, &deferred);
       // pins removed by this pass: positions with a non-diagonal op
       uint64_t nd = 0;
       for (const HOp* o : taken)
@@ -501,8 +694,18 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
         int q = 0;
         for (int lb = 0; lb < k; lb++)
           if ((Sreg >> lb) & 1) st.rbit[q++] = (int8_t)lb;
+        {
+          int t = 0;
+          for (int lb = 0; lb < k; lb++)
+            if (!((Sreg >> lb) & 1)) {
+              st.tpos[t] = (int8_t)lb;
+              st.tg[t] = dp.gpos[lb];
+              t++;
+            }
+          if (t > 8) fail(SF_EINVAL, "internal: more than 256 threads per tile");
+        }
         st.op_begin = (int)pp.ops.size();
-        if (!emit_stage_ops(st_ops, st, local_of, pp)) {
+        if (!emit_stage_ops(st_ops, st, local_of, dp.gpos, pp)) {
           ok = false;
           break;
         }
@@ -830,6 +1033,76 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
     throw;
   }
   return P;
+}
+
+static const char* op_name(int code) {
+  switch (code) {
+    case DOP_H: return "H";
+    case DOP_XH: return "X";
+    case DOP_YH: return "Y";
+    case DOP_G1: return "U1";
+    case DOP_G1SEL: return "XT";
+    case DOP_G2: return "U2";
+    case DOP_PHASE: return "PH";
+    case DOP_DMUL: return "D";
+    default: return "?";
+  }
+}
+
+std::string plan_describe(const Plan& p) {
+  std::string o;
+  char b[256];
+  snprintf(b, sizeof b, "qubits %d (grid %dx%d), half A %d, half B %d, cross gates %zu, path bits %d, levels %zu\n",
+           p.circ.n, p.circ.rows, p.circ.cols, p.A.m, p.B.m, p.cross.size(), p.path_bits, p.levels.size());
+  o += b;
+  for (size_t l = 0; l < p.levels.size(); l++) {
+    snprintf(b, sizeof b, "level %zu: cycle %d, %d cross gates, %d bits\n", l + 1, p.levels[l].cycle,
+             p.levels[l].n_cross, p.levels[l].bits);
+    o += b;
+  }
+  snprintf(b, sizeof b, "last level folded into the gather: %s; tile bits %d, fusion bits %d\n",
+           p.deferred ? "yes" : "no", p.tile_bits, p.fuse_bits);
+  o += b;
+  for (int side = 0; side < 2; side++) {
+    const HalfPlan& H = side ? p.B : p.A;
+    const int nseg = (int)H.seg.size() + (p.deferred ? 1 : 0);
+    for (int s = 0; s < nseg; s++) {
+      const SegmentPlan& sp = s < (int)H.seg.size() ? H.seg[s] : H.last_deferred;
+      snprintf(b, sizeof b, "half %c segment %d%s: %zu passes\n", side ? 'B' : 'A', s,
+               s == (int)H.seg.size() ? " (folded last level)" : "", sp.passes.size());
+      o += b;
+      for (size_t q = 0; q < sp.passes.size(); q++) {
+        const PassPlan& pp = sp.passes[q];
+        std::string act;
+        for (int j = 0; j < pp.dev.k; j++) act += std::to_string(pp.dev.gpos[j]) + (j + 1 < pp.dev.k ? "," : "");
+        snprintf(b, sizeof b, "  pass %zu: active [%s] pins in %d out %d%s scale 2^%d\n", q, act.c_str(),
+                 pp.dev.n_pin_in, pp.dev.n_pin_out, pp.dev.gen_input ? " generated" : "",
+                 (int)std::lround(std::log2(pp.dev.post_scale)));
+        o += b;
+        for (size_t t = 0; t < pp.stages.size(); t++) {
+          const DevStage& st = pp.stages[t];
+          std::string rb, ops;
+          for (int j = 0; j < st.r; j++) rb += std::to_string(pp.dev.gpos[st.rbit[j]]) + (j + 1 < st.r ? "," : "");
+          for (int x = st.op_begin; x < st.op_end; x++) {
+            const DevOp& d = pp.ops[x];
+            ops += op_name(d.code);
+            if (d.code == DOP_PHASE) {
+              const DevPhaseGroup& g = pp.phases[d.arg];
+              int ncz = 0;
+              for (int j = 0; j < st.r; j++) ncz += __builtin_popcount(g.czq[j]) + __builtin_popcount(g.czf[j]) * 2;
+              ops += "(" + std::to_string(g.nsh) + "sh," + std::to_string(g.nsel) + "sel)";
+            } else if (d.code != DOP_DMUL) {
+              ops += std::to_string(d.a);
+            }
+            ops += " ";
+          }
+          snprintf(b, sizeof b, "    stage %zu regs [%s]: %s\n", t, rb.c_str(), ops.c_str());
+          o += b;
+        }
+      }
+    }
+  }
+  return o;
 }
 
 void plan_destroy(Plan* p) {

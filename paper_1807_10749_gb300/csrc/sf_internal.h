@@ -54,6 +54,7 @@ constexpr int MAX_OPS = 160;
 constexpr int MAX_PHASE_GROUPS = 40;
 constexpr int MAX_CZ_PER_GROUP = 40;
 constexpr int MAX_SEL_PER_GROUP = 8;
+constexpr int MAX_SHIFTS = 16;
 constexpr int MAX_MATS = 640;      // float2 entries of matrices per pass
 constexpr int MAX_NODES = 128;     // nodes per pass launch
 constexpr int MAX_CROSS = 64;
@@ -81,18 +82,25 @@ struct DevOp {
   int32_t arg;
 };
 
-// A group of diagonal gates whose product is exp(i pi/4 * k(idx)) with
-//   k = popc(idx&m1) + 2 popc(idx&m2) + 4 popc(idx&m4)
-//       + 4 sum_pairs bit(p0) bit(p1) + sum_sel w_sel(digit) bit(pos)   (mod 8)
-// idx = the global index inside the half state.
+// A group of diagonal gates whose product is exp(i pi/4 * k(idx)), idx the
+// global index inside the half state, prepared for one register stage: with
+// idx = gfix | (register bits), k is a quadratic form in the register bits
+//   k = k0(gfix) + sum_j w_j i_j + 4 sum_{j<l, partners} i_j i_l   (mod 8)
+//   k0 = popc(gfix&m1) + 2 popc(gfix&m2) + 4 popc(gfix&m4)
+//        + 4 sum_s popc(gfix & (gfix >> sh_s) & shm_s) + [selected weights]
+//   w_j = wstat_j + 4 popc(gfix & czf_j) + [selected weights]
 struct DevPhaseGroup {
-  uint32_t m1, m2, m4;
-  int32_t ncz;
-  int8_t cz[MAX_CZ_PER_GROUP][2];
-  int32_t nsel;
+  uint32_t m1, m2, m4;       // weights (bits 1,2,4) of the fixed positions
+  uint8_t wstat[MAX_R];      // weight of register bit j from one-qubit phases
+  uint8_t czq[MAX_R];        // CZ partners of register bit j among register bits
+  uint32_t czf[MAX_R];       // CZ partners of register bit j among fixed positions
+  int32_t nsh;               // CZ pairs between fixed positions, by shift
+  uint8_t sh[MAX_SHIFTS];
+  uint32_t shm[MAX_SHIFTS];
+  int32_t nsel;              // path-selected phases (the B-side Z^b of Eq. 1)
   struct {
-    int8_t pos, xi;
-    uint8_t w[4];  // weight per digit value
+    int8_t pos, xi, reg;     // reg: register bit index or -1
+    uint8_t w[4];            // weight per digit value
   } sel[MAX_SEL_PER_GROUP];
 };
 
@@ -105,6 +113,8 @@ struct DevPin {
 struct DevStage {
   int32_t r;
   int8_t rbit[MAX_R];  // tile-local bit index of register bit j
+  int8_t tpos[8];      // tile-local bit of thread-index bit i (k - r of them)
+  int8_t tg[8];        // global position of thread-index bit i
   int32_t op_begin, op_end;
 };
 
@@ -188,7 +198,7 @@ struct Pin {
 // Host-side op of a half (positions are layout positions).
 enum HopKind { H_G1, H_G2, H_CZ, H_PHASE1, H_DMUL, H_XSEL, H_XPHASE, H_PROJ };
 struct HOp {
-  int kind;
+  int kind = -1;
   int p0 = -1, p1 = -1;
   int fast = 0;       // DOP_H / DOP_XH / DOP_YH for H_G1 with that matrix
   int scale_e = 0;    // deferred factor (1/sqrt2)^scale_e of the fast form
@@ -287,6 +297,7 @@ struct Plan {
 };
 
 Plan* plan_create(const Circuit& c, const sf_plan_opts& o);
+std::string plan_describe(const Plan& p);
 void plan_destroy(Plan* p);
 
 // ------------------------------------------------------------- selection
@@ -318,6 +329,7 @@ void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, 
 void exec_free_cache(void* cache);
 void ensure_device(Plan& p);
 void exec_release_cache(Plan& p);
+double segment_bytes(const SegmentPlan& s);  // algorithmic bytes of one node
 void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out);
 void prof_end(Plan& p, void* e1, void* stream);
 void prof_collect(Plan& p);

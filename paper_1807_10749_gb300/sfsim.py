@@ -27,7 +27,8 @@ EXPORTED = [
     "sf_selection_size", "sf_selection_ids", "sf_amplitudes", "sf_workspace_size",
     "sf_amplitudes_device", "sf_server_create", "sf_server_submit", "sf_server_wait",
     "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_plan_profile",
-    "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_last_error",
+    "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_plan_segment_stats",
+    "sf_plan_describe", "sf_last_error",
 ]
 
 
@@ -92,6 +93,8 @@ def lib():
             "sf_plan_profile": (i32, [P, i32]),
             "sf_plan_profile_read": (i32, [P, i32, P, P, P]),
             "sf_amplitudes_device_noalloc": (i32, [P, P, i64, P, P, i32, P]),
+            "sf_plan_segment_stats": (i32, [P, i32, i32, P, P, P]),
+            "sf_plan_describe": (i32, [P, P, ctypes.c_size_t, P]),
             "sf_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -162,6 +165,21 @@ def sf_plan_stats(plan):
     v = [ctypes.c_int() for _ in range(5)]
     _check(lib().sf_plan_stats(plan, *[ctypes.byref(x) for x in v]))
     return dict(zip(["passes_a", "passes_b", "stages_a", "stages_b", "deferred"], [x.value for x in v]))
+
+
+def sf_plan_segment_stats(plan, half, segment):
+    """(passes, stages, algorithmic bytes per node) of one segment of one half."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().sf_plan_segment_stats(plan, half, segment, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sf_plan_describe(plan) -> str:
+    n = ctypes.c_size_t()
+    _check(lib().sf_plan_describe(plan, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(lib().sf_plan_describe(plan, buf, n.value + 1, ctypes.byref(n)))
+    return buf.value.decode()
 
 
 def sf_plan_destroy(plan):
