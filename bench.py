@@ -209,6 +209,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--exec-mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--workload", default=WORKLOAD, choices=["7x8_d40", "5x10_d16"])
+    ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--fuse-bits", type=int, default=0)
+    ap.add_argument("--run-bits", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -237,7 +240,8 @@ def main():
     nq = w["rows"] * w["cols"]
     bits = inputs.random_bitstrings(nq, args.bitstrings, w["bitstring_seed"])
     mode = sfsim.SF_EXEC_PLAIN if args.exec_mode == "plain" else sfsim.SF_EXEC_BATCHED
-    plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode)
+    plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode, tile_bits=args.tile_bits,
+                      fuse_bits=args.fuse_bits, run_bits=args.run_bits)
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
     n_steps_total = args.warmup + args.steps
@@ -311,6 +315,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
+                                              "tile_bits": args.tile_bits or 13, "fuse_bits": args.fuse_bits or 5,
+                                              "run_bits": args.run_bits or 3,
                                               "paths_selected": n_sel, "parallelism": f"paths x{world}",
                                               "wall_s": wall}),
             "roofline": {"kernel": "pass_kernel (fused tile pass)", "bound": "hbm",

@@ -104,7 +104,9 @@ typedef struct {
   int64_t hbm_budget_bytes;  /* device memory the executor may use, 0 = 75% of
                                 free memory at plan time */
   int32_t batch_paths;       /* max leaf groups per launch, 0 = from budget */
-  int32_t reserved[7];
+  int32_t run_bits;          /* log2 contiguous amplitudes per copy run (the
+                                index bits every pass keeps active), 0 = 3 */
+  int32_t reserved[6];
 } sf_plan_opts;
 
 SF_API void sf_plan_opts_default(sf_plan_opts* o);
@@ -181,6 +183,20 @@ SF_API int sf_workspace_size(const sf_plan* p, int64_t n, const sf_path_sel* sel
 SF_API int sf_amplitudes_device(sf_plan* p, const uint64_t* d_bitstrings, int64_t n, const sf_path_sel* sel,
                          double* d_out_amps, int accumulate, void* d_workspace, size_t ws_bytes,
                          void* cuda_stream);
+
+/* Frugal rejection sampling, the accept step of Algorithm 2 (Section 4):
+ * candidate j (a uniformly drawn bitstring whose amplitude is d_amps[2j],
+ * d_amps[2j+1], e.g. the output of sf_amplitudes_device) is accepted iff
+ *   d_uniform[j] < min(1, t_j),  t_j = ((re^2 + im^2) * prob_scale) * N / mprime
+ * evaluated in FP64 in exactly this order without fused multiply-adds, so the
+ * decision is reproducible on the host. N = 2^n (qubits), mprime = M' (10 in
+ * the paper), prob_scale = 1, or 1/f_actual to renormalise a truncated path
+ * sum. d_uniform: n doubles in [0, 1) supplied by the caller. d_accept: n
+ * bytes, 1 = accepted; d_count: one int64, set to the number accepted. All
+ * pointers are device pointers; the work is enqueued on cuda_stream. */
+SF_API int sf_frugal_accept_device(const double* d_amps, const double* d_uniform, int64_t n, double N,
+                                   double mprime, double prob_scale, uint8_t* d_accept, int64_t* d_count,
+                                   void* cuda_stream);
 
 /* Fixed-scratch form of sf_amplitudes_device. This call has no counterpart
  * in the paper; it exists for callers that must not allocate device memory

@@ -144,6 +144,7 @@ int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out)
   if (o.exec_mode != SF_EXEC_BATCHED && o.exec_mode != SF_EXEC_PLAIN) sf::fail(SF_EINVAL, "unknown exec mode");
   if (o.tile_bits < 0 || o.tile_bits > sf::MAX_K) sf::fail(SF_EINVAL, "tile_bits out of range (0..14)");
   if (o.fuse_bits < 0 || o.fuse_bits > sf::MAX_R) sf::fail(SF_EINVAL, "fuse_bits out of range (0..5)");
+  if (o.run_bits < 0 || o.run_bits > 8) sf::fail(SF_EINVAL, "run_bits out of range (0..8)");
   if (o.hbm_budget_bytes < 0 || o.batch_paths < 0) sf::fail(SF_EINVAL, "negative budget or batch");
   if (o.exec_mode == SF_EXEC_PLAIN) {
     o.defer_last_level = 0;
@@ -321,6 +322,17 @@ int sf_amplitudes_device(sf_plan* h, const uint64_t* d_bits, int64_t n, const sf
   if (n > 0 && (!d_bits || !d_out)) sf::fail(SF_EINVAL, "null device buffer");
   ensure_device(*h->p);
   sf::exec_run(*h->p, d_bits, n, *sel, d_out, accumulate, d_ws, ws_bytes, stream, true);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_frugal_accept_device(const double* d_amps, const double* d_u, int64_t n, double N, double mprime,
+                            double prob_scale, uint8_t* d_accept, int64_t* d_count, void* stream) {
+  SF_GUARD_BEGIN
+  if (n < 0) sf::fail(SF_EINVAL, "negative count");
+  if (!d_count || (n > 0 && (!d_amps || !d_u || !d_accept))) sf::fail(SF_EINVAL, "null device buffer");
+  if (!(N > 0) || !(mprime > 0) || !(prob_scale > 0)) sf::fail(SF_EINVAL, "N, M' and the scale must be positive");
+  sf::launch_frugal(d_amps, d_u, n, N, mprime, prob_scale, d_accept, d_count, stream);
   return SF_OK;
   SF_GUARD_END
 }

@@ -218,15 +218,12 @@ __device__ __forceinline__ uint32_t pin_val(const DevPin& p, const uint8_t* xshi
 
 }  // namespace
 
-// ---- TMA bulk copies and mbarriers (inline PTX) ---------------------------
+// ---- mbarriers and asynchronous copies (inline PTX) ------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 // Wait for phase `parity` of the barrier, giving up after ~2^31 cycles.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
@@ -242,19 +239,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (clock64() - t0 > (1ll << 31)) return false;
   }
 }
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Per-item geometry: tile base index and pin masks (tile-local and run-level).
 struct ItemGeo {
@@ -300,26 +284,6 @@ __device__ __forceinline__ ItemGeo item_geo(const PassLaunch& P, int64_t item, i
     }
   }
   return g;
-}
-
-// Issue the TMA loads of one item's live runs into buffer `dst` (warp 0).
-__device__ __forceinline__ void issue_loads(const PassLaunch& P, const ItemGeo& g, const uint32_t* runoff,
-                                            uint32_t dst, uint32_t bar, int lane) {
-  const DevPass& d = P.pass;
-  const int L = d.L, nruns = 1 << (d.k - L);
-  const uint32_t rm = g.lin_m >> L, rv = g.lin_v >> L;
-  const uint32_t run_bytes = 8u << L;
-  if (lane == 0) {
-    const uint32_t live = d.gen_input ? 0u : ((uint32_t)nruns >> __popc(rm));
-    mbar_arrive_tx(bar, live * run_bytes);
-  }
-  __syncwarp();
-  if (d.gen_input) return;
-  const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
-  for (int r = lane; r < nruns; r += 32) {
-    if (((uint32_t)r & rm) != rv) continue;
-    bulk_g2s(dst + (uint32_t)r * run_bytes, in + (g.base | runoff[r]), run_bytes, bar);
-  }
 }
 
 __device__ __forceinline__ void compute_bar(int nthreads) {
@@ -441,18 +405,26 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
   }
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// the barrier's pending count drops by one when this thread's earlier
+// cp.async copies have landed
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
 // Persistent fused pass, warp-specialised. Each CTA walks work items
 // (node, tile) with stride gridDim.x through NBUF shared-memory tile buffers.
-// The last warp is the producer: it moves tiles between global and shared
-// memory as runs of 2^L contiguous amplitudes with TMA bulk copies (loads
-// complete on full[b]; a buffer's outgoing stores are issued once the compute
-// warps arrive on empty[b]). The compute warps run the register stages and
-// synchronise only among themselves (named barrier 1), so copies and gates
-// overlap. Input-pinned (structurally zero) runs are never read and
-// output-pinned runs never written. Every wait is bounded; a timeout sets the
-// error flag and ends the kernel.
+// Warp roles: compute warps run the register stages; a load warp streams the
+// next tiles in with 16-byte cp.async copies (one warp instruction moves 512
+// contiguous-run bytes; completion arrives on full[b]); a store warp streams
+// finished tiles out with 16-byte vector stores once the compute warps arrive
+// on empty[b], then frees the buffer (free[b]). Input-pinned (structurally
+// zero) runs are never read and output-pinned runs never written. Every wait
+// is bounded; a timeout sets the error flag and ends the kernel.
 template <int R, bool GEN>
-__global__ void __launch_bounds__(288, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
+__global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
   constexpr int NBUF = 3;
   extern __shared__ __align__(128) unsigned char smem[];
   const DevPass& d = P.pass;
@@ -465,17 +437,18 @@ __global__ void __launch_bounds__(288, 1) pass_kernel(const __grid_constant__ Pa
   uint32_t* runoff = reinterpret_cast<uint32_t*>(bufs + NBUF * ntile);
   uint64_t* full = reinterpret_cast<uint64_t*>(runoff + ((nruns + 1) & ~1));
   uint64_t* empty = full + NBUF;
+  uint64_t* freeb = empty + NBUF;
   __shared__ float2 w8[8];
   __shared__ int abort_flag;
   const int tiles_log2 = d.n_free;
   const int64_t items = (int64_t)P.n_nodes << tiles_log2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t run_bytes = 8u << L;
+  const int nchunk = ntile >> 1;                  // 16-byte chunks per tile
+  const int lmask = (1 << L) - 1;
 
   if (threadIdx.x < 8) {
     const float r = 0.70710678118654752f;
     const float c = (threadIdx.x & 1) ? r : 1.0f;
-    // e^{i pi t/4}: (cos, sin) from the octant
     const int t = threadIdx.x;
     float re = (t == 0) ? 1.f : (t == 2 || t == 6) ? 0.f : (t == 4) ? -1.f : (t == 1 || t == 7) ? c : -c;
     float im = (t == 2) ? 1.f : (t == 6) ? -1.f : (t == 0 || t == 4) ? 0.f : (t == 1 || t == 3) ? c : -c;
@@ -489,50 +462,68 @@ __global__ void __launch_bounds__(288, 1) pass_kernel(const __grid_constant__ Pa
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int b = 0; b < NBUF; b++) {
-      mbar_init(smem_u32(&full[b]), 1);
+      mbar_init(smem_u32(&full[b]), 32);
       mbar_init(smem_u32(&empty[b]), ncw);
+      mbar_init(smem_u32(&freeb[b]), 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
   if (warp == ncw) {
-    // ------------------------------------------------------------ producer
+    // --------------------------------------------------------------- loads
     int i = 0;
-    bool ok = true;
-    for (int64_t it = blockIdx.x; it < items + (int64_t)NBUF * gridDim.x && ok; it += gridDim.x, i++) {
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
       const int b = i % NBUF;
-      const uint32_t src = smem_u32(bufs + b * ntile);
-      if (i >= NBUF) {
-        // the item that used buffer b before: wait until computed, store it
-        const int64_t prev = it - (int64_t)NBUF * gridDim.x;
-        if (prev < items) {
-          if (!mbar_wait(smem_u32(&empty[b]), (uint32_t)((i / NBUF - 1) & 1)) || *(volatile int*)&abort_flag) {
-            ok = false;
-            break;
-          }
-          const ItemGeo g = item_geo(P, prev, tiles_log2);
-          float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
-          const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
-          for (int r = lane; r < nruns; r += 32) {
-            if (((uint32_t)r & rm) != rv) continue;
-            bulk_s2g(out + (g.base | runoff[r]), src + (uint32_t)r * run_bytes, run_bytes);
-          }
-          bulk_commit();
-          bulk_wait_read0();
-          __syncwarp();
+      if (i >= NBUF && !mbar_wait(smem_u32(&freeb[b]), (uint32_t)((i / NBUF - 1) & 1))) {
+        if (lane == 0) {
+          abort_flag = 1;
+          atomicExch(P.err, 1);
+        }
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      if (!d.gen_input) {
+        const ItemGeo g = item_geo(P, it, tiles_log2);
+        const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
+        const uint32_t dst = smem_u32(bufs + b * ntile);
+        const uint32_t rm = g.lin_m >> L, rv = g.lin_v >> L;
+        for (int c = lane; c < nchunk; c += 32) {
+          const int e = c << 1, r = e >> L;
+          if (((uint32_t)r & rm) != rv) continue;
+          cp_async16(dst + (uint32_t)e * 8u, in + (g.base | runoff[r] | (uint32_t)(e & lmask)));
         }
       }
-      if (it < items) {
-        fence_async_smem();
-        issue_loads(P, item_geo(P, it, tiles_log2), runoff, src, smem_u32(&full[b]), lane);
+      cp_async_arrive(smem_u32(&full[b]));
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    return;
+  }
+  if (warp == ncw + 1) {
+    // -------------------------------------------------------------- stores
+    int i = 0;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
+      const int b = i % NBUF;
+      if (!mbar_wait(smem_u32(&empty[b]), (uint32_t)((i / NBUF) & 1)) || *(volatile int*)&abort_flag) {
+        if (lane == 0) {
+          abort_flag = 1;
+          atomicExch(P.err, 1);
+        }
+        break;
       }
+      const ItemGeo g = item_geo(P, it, tiles_log2);
+      float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
+      const float4* src = reinterpret_cast<const float4*>(bufs + b * ntile);
+      const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
+      for (int c = lane; c < nchunk; c += 32) {
+        const int e = c << 1, r = e >> L;
+        if (((uint32_t)r & rm) != rv) continue;
+        const float4 v = src[c];
+        *reinterpret_cast<float4*>(out + (g.base | runoff[r] | (uint32_t)(e & lmask))) = v;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&freeb[b]));
     }
-    if (!ok && lane == 0) {
-      abort_flag = 1;
-      atomicExch(P.err, 1);
-    }
-    bulk_wait0();
     return;
   }
 
@@ -567,9 +558,8 @@ __global__ void __launch_bounds__(288, 1) pass_kernel(const __grid_constant__ Pa
         float2 v = sm[e];
         sm[e] = make_float2(v.x * d.post_scale, v.y * d.post_scale);
       }
+      compute_bar(ncomp);
     }
-    // hand the buffer to the producer: generic writes -> async proxy
-    fence_async_smem();
     __syncwarp();
     if (lane == 0) mbar_arrive(smem_u32(&empty[b]));
   }
@@ -700,6 +690,23 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
   }
 }
 
+// Accept step of frugal rejection sampling (Section 4, Algorithm 2), in the
+// operation order documented in sfsim.h, without contraction.
+__global__ void frugal_accept_kernel(const double* amps, const double* u, int64_t n, double N, double mp,
+                                     double scale, uint8_t* acc, unsigned long long* count) {
+  unsigned long long mine = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double re = amps[2 * i], im = amps[2 * i + 1];
+    const double p = __dmul_rn(__dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)), scale);
+    const double t = __ddiv_rn(__dmul_rn(p, N), mp);
+    const bool a = u[i] < fmin(1.0, t);
+    acc[i] = a ? 1 : 0;
+    mine += a ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
+}
+
 __global__ void zero_kernel(double* p, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = 0.0;
@@ -724,9 +731,9 @@ static int num_sms() {
 template <int R, bool GEN>
 static void launch_pass_r(const PassLaunch& L, int tiles, int tile_k, cudaStream_t s) {
   const int nact = 1 << (tile_k - R);
-  const int threads = ((nact + 31) / 32) * 32 + 32;  // compute warps + the producer warp
+  const int threads = ((nact + 31) / 32) * 32 + 64;  // compute warps + load and store warps
   const int nruns = 1 << (tile_k - L.pass.L);
-  const size_t smem = 3 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 6 * 8;
+  const size_t smem = 3 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 9 * 8;
   // The dynamic shared-memory limit is a property of the kernel function, so
   // it only ever grows; occupancy is cached per tile size.
   static std::mutex mu;
@@ -804,6 +811,17 @@ void launch_zero(double* p, int64_t n, void* stream) {
   if (blocks > 4096) blocks = 4096;
   zero_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(p, n);
   check(cudaGetLastError(), "zero_kernel launch");
+}
+
+void launch_frugal(const double* amps, const double* u, int64_t n, double N, double mp, double scale,
+                   uint8_t* acc, int64_t* count, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  check(cudaMemsetAsync(count, 0, sizeof(int64_t), s), "cudaMemsetAsync");
+  if (n <= 0) return;
+  int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+  frugal_accept_kernel<<<(int)blocks, 256, 0, s>>>(amps, u, n, N, mp, scale, acc,
+                                                    reinterpret_cast<unsigned long long*>(count));
+  check(cudaGetLastError(), "frugal_accept_kernel launch");
 }
 
 }  // namespace sf

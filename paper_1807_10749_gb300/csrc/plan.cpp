@@ -261,7 +261,7 @@ bool finish_group(const GroupAcc& acc, const int* gr, int R, DevPhaseGroup& g) {
   for (int p = 0; p < 32; p++) {
     int w = ((acc.w[p] % 8) + 8) % 8;
     if ((rmask >> p) & 1u) {
-      for (int j = 0; j < R; j++)
+      for (int j = 0; j < R && j < MAX_R; j++)
         if (gr[j] == p) g.wstat[j] = (uint8_t)w;
       continue;
     }
@@ -471,7 +471,7 @@ DevPin to_dev(const Pin& p) {
 
 // Plan one segment of one half into passes. ops are consumed in order.
 void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins, bool gen_input,
-                  int tile_bits, int fuse_bits, SegmentPlan& out) {
+                  int tile_bits, int fuse_bits, int run_bits, SegmentPlan& out) {
   std::vector<const HOp*> rem;
   for (auto& o : seg_ops) {
     if (o.kind == H_PROJ) {
@@ -485,7 +485,7 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
     }
   }
   const int k = std::min(tile_bits, m);
-  const int L = std::min(4, k);
+  const int L = std::max(1, std::min(run_bits, k));
   // register bits: at most the fusion width, at least enough that a tile
   // needs no more than 256 threads, and leave >= 2^min(5,k-1) threads per tile
   int R = std::max(1, std::min(fuse_bits, k - std::min(5, k - 1)));
@@ -767,6 +767,7 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
     // pass kernel holds at most 13 tile bits
     P->tile_bits = o.tile_bits > 0 ? std::min(o.tile_bits, 13) : 13;
     P->fuse_bits = o.fuse_bits > 0 ? std::min(o.fuse_bits, MAX_R) : 5;
+    P->run_bits = o.run_bits > 0 ? std::min(o.run_bits, 8) : 3;
     if (P->tile_bits < 6) P->tile_bits = 6;
 
     // cross gates in time order (cycle, lower qubit, higher qubit)
@@ -1000,13 +1001,13 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
       H.seg.assign(nL + 1, SegmentPlan());
       std::vector<Pin> pins = H.root_pins;
       for (int s = 0; s <= nL; s++) {
-        plan_segment(H.m, H.seg_ops[s], pins, s == 0, P->tile_bits, P->fuse_bits, H.seg[s]);
+        plan_segment(H.m, H.seg_ops[s], pins, s == 0, P->tile_bits, P->fuse_bits, P->run_bits, H.seg[s]);
         H.seg[s].scale *= seg_global[2 * s + side];
         pins = H.seg[s].pins_out;
       }
       if (P->deferred) {
         std::vector<Pin> pin_in = nL >= 1 ? H.seg[nL - 1].pins_out : H.root_pins;
-        plan_segment(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, P->tile_bits, P->fuse_bits,
+        plan_segment(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, P->tile_bits, P->fuse_bits, P->run_bits,
                      H.last_deferred);
         H.last_deferred.scale *= seg_global[2 * nL + side];
       }

@@ -286,7 +286,7 @@ struct Plan {
   int defer_bits = 0;          // bits of the last level when deferred
   float ma[MAX_DEFER][4][8];
   float mb[MAX_DEFER][4][8];
-  int tile_bits = 13, fuse_bits = 5;
+  int tile_bits = 13, fuse_bits = 5, run_bits = 3;
   // device copies
   uint32_t* d_tabA = nullptr;
   uint32_t* d_tabB = nullptr;
@@ -339,6 +339,8 @@ void prof_release(Plan& p);
 void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, void* stream);
 void launch_gather(const GatherLaunch& L, void* stream);
 void launch_zero(double* p, int64_t n_doubles, void* stream);
+void launch_frugal(const double* amps, const double* u, int64_t n, double N, double mp, double scale,
+                   uint8_t* acc, int64_t* count, void* stream);
 
 }  // namespace sf
 

@@ -28,7 +28,7 @@ EXPORTED = [
     "sf_amplitudes_device", "sf_server_create", "sf_server_submit", "sf_server_wait",
     "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_plan_profile",
     "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_plan_segment_stats",
-    "sf_plan_describe", "sf_last_error",
+    "sf_plan_describe", "sf_frugal_accept_device", "sf_last_error",
 ]
 
 
@@ -48,7 +48,8 @@ class sf_plan_opts(ctypes.Structure):
                 ("select_prefix_bits", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
                 ("fuse_bits", ctypes.c_int32), ("exec_mode", ctypes.c_int32),
                 ("defer_last_level", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
-                ("batch_paths", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("batch_paths", ctypes.c_int32), ("run_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class sf_path_sel(ctypes.Structure):
@@ -95,6 +96,8 @@ def lib():
             "sf_amplitudes_device_noalloc": (i32, [P, P, i64, P, P, i32, P]),
             "sf_plan_segment_stats": (i32, [P, i32, i32, P, P, P]),
             "sf_plan_describe": (i32, [P, P, ctypes.c_size_t, P]),
+            "sf_frugal_accept_device": (i32, [P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              P, P, P]),
             "sf_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -299,6 +302,19 @@ def sf_plan_profile_read(plan, kernel):
     n, t, b = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
     _check(lib().sf_plan_profile_read(plan, kernel, ctypes.byref(n), ctypes.byref(t), ctypes.byref(b)))
     return n.value, t.value, b.value
+
+
+def sf_frugal_accept_device(d_amps, d_uniform, n_qubits, mprime, d_accept, d_count, prob_scale=1.0,
+                            stream=None):
+    """Accept step of frugal rejection sampling on device tensors: d_amps
+    float64 (n, 2), d_uniform float64 (n,), d_accept uint8 (n,), d_count int64 (1,)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().sf_frugal_accept_device(ctypes.c_void_p(d_amps.data_ptr()), ctypes.c_void_p(d_uniform.data_ptr()),
+                                         d_uniform.numel(), float(2.0 ** n_qubits), float(mprime),
+                                         float(prob_scale), ctypes.c_void_p(d_accept.data_ptr()),
+                                         ctypes.c_void_p(d_count.data_ptr()), ctypes.c_void_p(stream.cuda_stream)))
 
 
 def sf_last_error() -> str:

@@ -231,3 +231,31 @@ def test_7x8_prefix_batched_equals_plain():
     check_close(a, b, 56, "7x8 prefix batched vs plain")
     p.close()
     q.close()
+
+
+# ----------------------------------------------- frugal sampling (Section 4)
+def test_frugal_accept_matches_oracle_bit_exactly():
+    """Algorithm 2's accept step on the GPU equals the oracle's decision on the
+    same amplitudes (5x6, all paths, 100k candidates), and the acceptance rate
+    is ~1/M' for Porter-Thomas probabilities."""
+    import torch
+    from oracle import sampling
+    w, text = workload("5x6_d24")
+    bits = inputs.random_bitstrings(30, w["n_bitstrings"], w["bitstring_seed"])
+    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    amp, _ = p.amplitudes(bits, sfsim.selection("fraction", fidelity=1.0))
+    p.close()
+    rng = np.random.default_rng(2)
+    u = rng.random(len(bits))
+    d_amps = torch.from_numpy(np.stack([amp.real, amp.imag], 1).copy()).cuda()
+    d_u = torch.from_numpy(u).cuda()
+    d_acc = torch.empty(len(bits), dtype=torch.uint8, device="cuda")
+    d_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sfsim.sf_frugal_accept_device(d_amps, d_u, 30, 10.0, d_acc, d_cnt)
+    torch.cuda.synchronize()
+    got = d_acc.cpu().numpy().astype(bool)
+    pr = (amp.real * amp.real + amp.imag * amp.imag) * 1.0
+    want = sampling.accept_frugal(pr, u, 2.0 ** 30, 10.0)
+    assert np.array_equal(got, want)
+    assert int(d_cnt.item()) == int(want.sum())
+    assert abs(want.mean() - 0.1) < 0.01

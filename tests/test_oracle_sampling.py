@@ -1,0 +1,45 @@
+"""Pins of the rejection-sampling oracle (Section 4, Algorithms 1 and 2)."""
+import math
+
+import numpy as np
+
+from oracle import circuit, sampling, sim
+from paper_1807_10749_gb300 import inputs
+
+
+def test_printed_constants():
+    # M = ceil(ln(10^3 * 2^49)) = 41 for eps = 1e-3, n = 49
+    assert sampling.basic_M(2.0 ** 49, 1e-3) == 41
+    # frugal, M' = 10: eps = e^-10 * 11 = 5e-4 (printed "5 * 10^-4")
+    assert abs(sampling.frugal_eps(10) - 4.994e-4) < 1e-6
+    # accepting high probabilities instead of dropping them: 9e-5 (printed)
+    assert abs(sampling.frugal_tv_no_drop(10) - 9.08e-5) < 1e-7
+
+
+def test_closed_forms_by_quadrature():
+    # e^{-M'}(1+M') = int_{M'}^inf t e^{-t} dt, numerically
+    t = np.linspace(10, 80, 700001)
+    assert abs(np.trapezoid(t * np.exp(-t), t) - sampling.frugal_eps(10)) < 1e-9
+
+
+def test_acceptance_rule_and_rate_on_porter_thomas():
+    """Exact 4x5 depth-40 probabilities (Porter-Thomas): the frugal sampler
+    accepts ~1/M' of the candidates, its dropped mass is ~e^{-M'}(1+M'), and
+    the accepted bitstrings follow p (heavier ones more often)."""
+    c = circuit.parse(inputs.google_circuit(4, 5, 40, 1).text())
+    N = 1 << c.n
+    p = np.abs(sim.sv_amplitudes(c, np.arange(N, dtype=np.uint64))) ** 2
+    rng = np.random.default_rng(5)
+    u = rng.random(N)
+    acc = sampling.accept_frugal(p, u, N, 10)
+    assert abs(acc.mean() - 0.1) < 0.005            # E[min(1, Np/10)] ~ 1/10
+    assert abs(sampling.dropped_mass(p, N, 10) - sampling.frugal_eps(10)) < 3e-4
+    # acceptance probability is monotone in p: heavier half accepted more
+    heavy = p > np.median(p)
+    assert acc[heavy].mean() > 3 * acc[~heavy].mean()
+    # basic sampler never accepts a dropped bitstring
+    M = 12
+    b = sampling.accept_basic(p, u, N, M)
+    assert not np.any(b & (p > M / N))
+    # a planted mistake (N p / M' replaced by p / M') accepts almost nothing
+    assert (u < np.minimum(1.0, p / 10)).mean() < 1e-3
