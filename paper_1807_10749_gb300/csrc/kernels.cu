@@ -240,6 +240,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
+// Shared-memory layout of a tile: element e lives at swz(e), a linear XOR
+// swizzle that folds index bits 4..12 into bits 1..3. It keeps 16-byte
+// chunks (element pairs) intact for the copy warps and, being linear,
+// swz(a ^ b) = swz(a) ^ swz(b), so register stages still step addresses with
+// one XOR per amplitude; it spreads the stages' strided accesses over the
+// shared-memory banks (at most two wavefronts per half-warp).
+__device__ __forceinline__ uint32_t swz(uint32_t e) {
+  const uint32_t x = e >> 4;
+  return e ^ (((x ^ (x >> 3) ^ (x >> 6)) & 7u) << 1);
+}
+
 // Per-item geometry: tile base index and pin masks (tile-local and run-level).
 struct ItemGeo {
   uint32_t base;                 // global index bits of the tile (inactive bits)
@@ -309,13 +320,12 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
   const int k = d.k;
   for (int s = 0; s < d.n_stages; s++) {
     const DevStage& st = P.stages[s];
-    int roff[R], gr[R];
-    uint32_t rl = 0;
+    uint32_t poff[R];
+    int gr[R];
 #pragma unroll
     for (int j = 0; j < R; j++) {
-      roff[j] = 1 << st.rbit[j];
+      poff[j] = swz(1u << st.rbit[j]);
       gr[j] = d.gpos[st.rbit[j]];
-      rl |= 1u << st.rbit[j];
     }
     uint32_t lfix = 0, gfix = g.base;
     for (int t = 0; t < k - R; t++) {
@@ -323,16 +333,15 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
       lfix |= b << st.tpos[t];
       gfix |= b << st.tg[t];
     }
-    (void)rl;
+    const uint32_t pfix = swz(lfix);
     float2 v[1 << R];
     {
-      int addr = (int)lfix;
+      uint32_t addr = pfix;
       v[0] = sm[addr];
 #pragma unroll
       for (int i = 1; i < (1 << R); i++) {
         const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
-        const int j = cctz(gi ^ prev);
-        addr += (gi & (1 << j)) ? roff[j] : -roff[j];
+        addr ^= poff[cctz(gi ^ prev)];
         v[gi] = sm[addr];
       }
     }
@@ -391,13 +400,12 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
     }
     const float sc = (s == d.n_stages - 1) ? post_scale : 1.0f;
     {
-      int addr = (int)lfix;
+      uint32_t addr = pfix;
       sm[addr] = make_float2(v[0].x * sc, v[0].y * sc);
 #pragma unroll
       for (int i = 1; i < (1 << R); i++) {
         const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
-        const int j = cctz(gi ^ prev);
-        addr += (gi & (1 << j)) ? roff[j] : -roff[j];
+        addr ^= poff[cctz(gi ^ prev)];
         sm[addr] = make_float2(v[gi].x * sc, v[gi].y * sc);
       }
     }
@@ -491,7 +499,7 @@ __global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ Pa
         for (int c = lane; c < nchunk; c += 32) {
           const int e = c << 1, r = e >> L;
           if (((uint32_t)r & rm) != rv) continue;
-          cp_async16(dst + (uint32_t)e * 8u, in + (g.base | runoff[r] | (uint32_t)(e & lmask)));
+          cp_async16(dst + swz((uint32_t)e) * 8u, in + (g.base | runoff[r] | (uint32_t)(e & lmask)));
         }
       }
       cp_async_arrive(smem_u32(&full[b]));
@@ -518,7 +526,7 @@ __global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ Pa
       for (int c = lane; c < nchunk; c += 32) {
         const int e = c << 1, r = e >> L;
         if (((uint32_t)r & rm) != rv) continue;
-        const float4 v = src[c];
+        const float4 v = src[swz((uint32_t)e) >> 1];
         *reinterpret_cast<float4*>(out + (g.base | runoff[r] | (uint32_t)(e & lmask))) = v;
       }
       __syncwarp();
@@ -543,11 +551,11 @@ __global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ Pa
     }
     if (d.gen_input) {
       for (int e = threadIdx.x; e < ntile; e += ncomp)
-        sm[e] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+        sm[swz(e)] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
       compute_bar(ncomp);
     } else if (g.lin_m) {
       for (int e = threadIdx.x; e < ntile; e += ncomp)
-        if (((uint32_t)e & g.lin_m) != g.lin_v) sm[e] = make_float2(0.f, 0.f);
+        if (((uint32_t)e & g.lin_m) != g.lin_v) sm[swz(e)] = make_float2(0.f, 0.f);
       compute_bar(ncomp);
     }
     if (threadIdx.x < nact) run_stages<R, GEN>(P, sm, g, w8, d.post_scale, ncomp);
