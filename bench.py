@@ -161,6 +161,72 @@ def max_over_ranks(value, device=None):
     return float(t.item())
 
 
+def serving_window(sfsim, inputs, n_req=24, seed=42, max_paths=1 << 17, load=0.8):
+    """Serving mix (time-boxed): requests drawn like the 2000-request stream -
+    grids uniform over 4x5, 5x5, 5x6, 6x6, 6x7, depth 1+d+1 with d uniform in
+    16..32, f log-uniform in [0.01, 1], 1e3..1e6 bitstrings log-uniform -
+    keeping the first n_req whose selected path count is <= max_paths (the
+    full stream is hours of work). Each request first runs alone, one after
+    the other (the plain form); then all are submitted to the server with
+    Poisson arrivals at `load` times the plain capacity. Returns latency
+    percentiles, aggregate paths/s both ways, and whether every served result
+    equals the request run alone."""
+    rng = np.random.default_rng(seed)
+    grids = [(4, 5), (5, 5), (5, 6), (6, 6), (6, 7)]
+    reqs = []
+    while len(reqs) < n_req:
+        R, C = grids[rng.integers(len(grids))]
+        d = int(rng.integers(16, 33))
+        f = float(np.exp(rng.uniform(np.log(0.01), 0.0)))
+        na = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
+        plan = sfsim.Plan(inputs.google_circuit(R, C, d, 1 + len(reqs)).text())
+        sel = sfsim.selection("fraction", fidelity=f, seed=7 + len(reqs))
+        npaths, _ = sfsim.sf_selection_size(plan.handle, sel)
+        if npaths > max_paths:
+            plan.close()
+            continue
+        bits = inputs.random_bitstrings(R * C, na, 2000 + len(reqs))
+        reqs.append((plan, bits, sel, npaths))
+    alone, t_alone = [], []
+    for plan, bits, sel, _ in reqs:
+        t0 = time.perf_counter()
+        alone.append(plan.amplitudes(bits, sel)[0])
+        t_alone.append(time.perf_counter() - t0)
+    paths = sum(r[3] for r in reqs)
+    t_seq = sum(t_alone)
+    rate = load * len(reqs) / t_seq
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    srv = sfsim.sf_server_create(0, 4)
+    tickets = []
+    t0 = time.perf_counter()
+    for (plan, bits, sel, _), ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append(sfsim.sf_server_submit(srv, plan.handle, bits, sel))
+    lat, same = [], True
+    for t, (plan, bits, sel, _), a in zip(tickets, reqs, alone):
+        while True:  # the server's own submit-to-done time, read before the wait releases it
+            try:
+                lat.append(sfsim.sf_server_times(srv, t)[1])
+                break
+            except sfsim.SFError as e:
+                if e.code != sfsim.SF_ETIMEOUT:
+                    raise
+                time.sleep(0.001)
+        got = sfsim.sf_server_wait(srv, t, len(bits))
+        same = same and bool(np.array_equal(got, a))
+    makespan = time.perf_counter() - t0
+    sfsim.sf_server_destroy(srv)
+    for plan, _, _, _ in reqs:
+        plan.close()
+    return {"requests": len(reqs), "paths": int(paths), "offered_load": load,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                  "plain_paths_per_s": paths / t_seq, "served_paths_per_s": paths / makespan,
+                  "served_identical_to_alone": same, "makespan_s": makespan, "plain_total_s": t_seq,
+            "window": f"first {n_req} requests of the seeded mix with <= {max_paths} paths"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores, same metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -207,6 +273,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--bitstrings", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--exec-mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--workload", default=WORKLOAD, choices=["7x8_d40", "5x10_d16"])
     ap.add_argument("--tile-bits", type=int, default=0)
@@ -302,6 +370,32 @@ def main():
     e2e_wall = max_over_ranks(time.perf_counter() - t1, f"cuda:{dev}")
     e2e_value = 128 * e2e_steps * world / e2e_wall
 
+    plain = None
+    if world == 1 and not args.no_plain and args.exec_mode == "batched":
+        # the plain form: the same kernels, one path at a time from the prefix
+        # checkpoint (no shared levels below it, no folded last level)
+        pplan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN,
+                           tile_bits=args.tile_bits, fuse_bits=args.fuse_bits, run_bits=args.run_bits)
+        pws = torch.empty(sfsim.sf_workspace_size(pplan.handle, len(bits), sels[0]), dtype=torch.uint8,
+                          device=f"cuda:{dev}")
+        sub = [sfsim.selection("range", first=int(prefixes[args.warmup]), count=16)]
+        sfsim.sf_amplitudes_device(pplan.handle, d_bits, sub[0], d_out, pws, stream=stream, accumulate=True)
+        torch.cuda.synchronize()
+        sub2 = sfsim.selection("range", first=int(prefixes[args.warmup]) + 16, count=32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sfsim.sf_amplitudes_device(pplan.handle, d_bits, sub2, d_out, pws, stream=stream, accumulate=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain = {"value": 32 / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                 "sample": "32 paths of the first timed prefix, each evolved alone from the resident "
+                           "prefix checkpoint (no shared levels below it, no folded last level)"}
+        del pws
+        pplan.close()
+    serving = None
+    if world == 1 and not args.no_serve and args.workload == WORKLOAD:
+        serving = serving_window(sfsim, inputs)
+
     if rank == 0:
         peak, peak_kind = measured_peaks()
         achieved = (pass_b / pass_s) / 1e9 if pass_s > 0 else None
@@ -333,6 +427,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(bits),
                     "d2h_bytes_per_step": 16 * len(bits), "steps": e2e_steps},
             "clocks": clocks,
+            "plain_form": plain,
+            "batched_over_plain": (value / plain["value"]) if plain else None,
+            "serving": serving,
             "cpu_baseline": ({k: v for k, v in cpu.items() if k != "seconds"} if cpu else None),
         }
         print(json.dumps(line), flush=True)

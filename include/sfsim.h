@@ -157,6 +157,16 @@ typedef struct {
   int64_t n_list;
 } sf_path_sel;
 
+/* Autotuner: plans the circuit with every candidate (tile_bits in {12, 13},
+ * fuse_bits in {4, 5}, run_bits in {3, 4, 5}) on top of *base, runs the first
+ * sample_paths paths of *sel for the n device bitstrings d_bits once to warm
+ * up and once timed (CUDA events, a private stream), and writes the fastest
+ * candidate's options to *best and its time to *best_seconds (may be NULL).
+ * Allocates and frees the device memory it needs. */
+SF_API int sf_plan_autotune(const sf_circuit* c, const sf_plan_opts* base, const sf_path_sel* sel,
+                            int64_t sample_paths, const uint64_t* d_bits, int64_t n, sf_plan_opts* best,
+                            double* best_seconds);
+
 /* Number of selected paths and f_actual = selected / 2^path_bits. */
 SF_API int sf_selection_size(const sf_plan* p, const sf_path_sel* sel, uint64_t* n_paths, double* f_actual);
 

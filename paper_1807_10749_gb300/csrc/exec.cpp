@@ -497,6 +497,16 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
       }
       run_segment(*C, plan, finA, jobsA, st, prof, err);
       run_segment(*C, plan, finB, jobsB, st, prof, err);
+      if (plan.opts.exec_mode == SF_EXEC_PLAIN) {
+        // the plain form shares nothing below the selection prefix: every
+        // path re-evolves its levels under the prefix checkpoint
+        int cum = 0;
+        for (int s = 0; s < nL; s++) {
+          if (cum > plan.xs)
+            for (auto& sl : C->slots[s]) sl.valid = false;
+          cum += plan.levels[s].bits;
+        }
+      }
       for (size_t g0 = 0; g0 < gf.size(); g0 += GATHER_FINALS) {
         size_t g1 = std::min(gf.size(), g0 + GATHER_FINALS);
         G.n_finals = (int)(g1 - g0);

@@ -28,7 +28,7 @@ EXPORTED = [
     "sf_amplitudes_device", "sf_server_create", "sf_server_submit", "sf_server_wait",
     "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_plan_profile",
     "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_plan_segment_stats",
-    "sf_plan_describe", "sf_frugal_accept_device", "sf_last_error",
+    "sf_plan_describe", "sf_frugal_accept_device", "sf_plan_autotune", "sf_last_error",
 ]
 
 
@@ -98,6 +98,7 @@ def lib():
             "sf_plan_describe": (i32, [P, P, ctypes.c_size_t, P]),
             "sf_frugal_accept_device": (i32, [P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               P, P, P]),
+            "sf_plan_autotune": (i32, [P, P, P, i64, P, i64, P, P]),
             "sf_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -183,6 +184,17 @@ def sf_plan_describe(plan) -> str:
     buf = ctypes.create_string_buffer(n.value + 1)
     _check(lib().sf_plan_describe(plan, buf, n.value + 1, ctypes.byref(n)))
     return buf.value.decode()
+
+
+def sf_plan_autotune(circuit, base: sf_plan_opts, sel, sample_paths, d_bits):
+    """Fastest (tile_bits, fuse_bits, run_bits) for this circuit and request
+    sample, timed on the device: returns (sf_plan_opts, seconds)."""
+    best = sf_plan_opts()
+    t = ctypes.c_double()
+    _check(lib().sf_plan_autotune(circuit, ctypes.byref(base), ctypes.byref(sel), sample_paths,
+                                  ctypes.c_void_p(d_bits.data_ptr()), d_bits.numel(), ctypes.byref(best),
+                                  ctypes.byref(t)))
+    return best, t.value
 
 
 def sf_plan_destroy(plan):
