@@ -217,6 +217,12 @@ def serving_window(sfsim, inputs, n_req=24, seed=42, max_paths=1 << 17, load=0.8
         got = sfsim.sf_server_wait(srv, t, len(bits))
         same = same and bool(np.array_equal(got, a))
     makespan = time.perf_counter() - t0
+    # closed loop: every request submitted at once (server capacity)
+    t1 = time.perf_counter()
+    tk = [sfsim.sf_server_submit(srv, plan.handle, bits, sel) for plan, bits, sel, _ in reqs]
+    for t, (plan, bits, sel, _) in zip(tk, reqs):
+        sfsim.sf_server_wait(srv, t, len(bits))
+    saturated = time.perf_counter() - t1
     sfsim.sf_server_destroy(srv)
     for plan, _, _, _ in reqs:
         plan.close()
@@ -224,6 +230,7 @@ def serving_window(sfsim, inputs, n_req=24, seed=42, max_paths=1 << 17, load=0.8
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                   "plain_paths_per_s": paths / t_seq, "served_paths_per_s": paths / makespan,
                   "served_identical_to_alone": same, "makespan_s": makespan, "plain_total_s": t_seq,
+            "saturated_paths_per_s": paths / saturated,
             "window": f"first {n_req} requests of the seeded mix with <= {max_paths} paths"}
 
 
