@@ -208,6 +208,15 @@ SF_API int sf_frugal_accept_device(const double* d_amps, const double* d_uniform
                                    double mprime, double prob_scale, uint8_t* d_accept, int64_t* d_count,
                                    void* cuda_stream);
 
+/* Fidelity estimate between two sets of amplitudes on the same bitstrings
+ * (Appendix C, the validation protocol; Section 3): with a = d_amps_a and
+ * b = d_amps_b (2n doubles each, interleaved), writes to d_out (4 doubles,
+ * device) Re and Im of sum_j conj(a_j) b_j, sum_j |a_j|^2 and sum_j |b_j|^2,
+ * accumulated in FP64. The estimate is f_e = |<a|b>|^2 / (<a|a> <b|b>).
+ * Enqueued on cuda_stream. */
+SF_API int sf_overlap_device(const double* d_amps_a, const double* d_amps_b, int64_t n, double* d_out,
+                             void* cuda_stream);
+
 /* Fixed-scratch form of sf_amplitudes_device. This call has no counterpart
  * in the paper; it exists for callers that must not allocate device memory
  * once they run (cudaMalloc may synchronise the device, and fails when

@@ -337,6 +337,14 @@ int sf_frugal_accept_device(const double* d_amps, const double* d_u, int64_t n, 
   SF_GUARD_END
 }
 
+int sf_overlap_device(const double* a, const double* b, int64_t n, double* out, void* stream) {
+  SF_GUARD_BEGIN
+  if (n < 0 || !out || (n > 0 && (!a || !b))) sf::fail(SF_EINVAL, "bad argument");
+  sf::launch_overlap(a, b, n, out, stream);
+  return SF_OK;
+  SF_GUARD_END
+}
+
 int sf_amplitudes(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel* sel, double* out,
                   double* f_actual) {
   SF_GUARD_BEGIN

@@ -45,214 +45,126 @@ __host__ __device__ constexpr int cctz(int v) {
   return r;
 }
 
-// ---- register blocks ------------------------------------------------------
-// A thread's 2^R amplitudes (register index i; bit j of i <-> register bit j
-// of the stage) are held as re/im pairs: Vr[s] = (re(2s), re(2s+1)),
-// Vi[s] = (im(2s), im(2s+1)). Register bit 0 is the "pair bit": gates on
-// register bits 1..R-1 pair slots s and s | 2^(j-1) lane by lane, so two
-// amplitudes move through one packed FP32x2 instruction (FADD2 / FMUL2 /
-// FFMA2). Gates on the pair bit mix the two lanes of a slot and run on
-// scalars; the planner puts a gate-free bit there when the stage has one.
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// scalar view of amplitude i (compile-time i)
-template <int I>
-__device__ __forceinline__ float2 amp_get(const float2* Vr, const float2* Vi) {
-  return (I & 1) ? make_float2(Vr[I >> 1].y, Vi[I >> 1].y) : make_float2(Vr[I >> 1].x, Vi[I >> 1].x);
-}
-template <int I>
-__device__ __forceinline__ void amp_set(float2* Vr, float2* Vi, float2 v) {
-  if (I & 1) {
-    Vr[I >> 1].y = v.x;
-    Vi[I >> 1].y = v.y;
-  } else {
-    Vr[I >> 1].x = v.x;
-    Vi[I >> 1].x = v.y;
-  }
-}
-
-// Packed one-qubit gates on register bit J >= 1 (slot bit J-1).
-// H: [[1,1],[1,-1]] (1/sqrt2 deferred)
-template <int R, int J>
-__device__ __forceinline__ void pk_h(float2* Vr, float2* Vi) {
-  constexpr int NS = 1 << (R - 1), SB = 1 << (J - 1);
-#pragma unroll
-  for (int s = 0; s < NS; s++) {
-    if (s & SB) continue;
-    const float2 ar = Vr[s], ai = Vi[s], br = Vr[s | SB], bi = Vi[s | SB];
-    Vr[s] = f2add(ar, br);
-    Vi[s] = f2add(ai, bi);
-    Vr[s | SB] = f2sub(ar, br);
-    Vi[s | SB] = f2sub(ai, bi);
-  }
-}
-// 2 X^1/2 = [[1+i, 1-i], [1-i, 1+i]]: out0 = s + i d, out1 = s - i d
-template <int R, int J>
-__device__ __forceinline__ void pk_xh(float2* Vr, float2* Vi) {
-  constexpr int NS = 1 << (R - 1), SB = 1 << (J - 1);
-#pragma unroll
-  for (int s = 0; s < NS; s++) {
-    if (s & SB) continue;
-    const float2 sr = f2add(Vr[s], Vr[s | SB]), si = f2add(Vi[s], Vi[s | SB]);
-    const float2 dr = f2sub(Vr[s], Vr[s | SB]), di = f2sub(Vi[s], Vi[s | SB]);
-    Vr[s] = f2sub(sr, di);
-    Vi[s] = f2add(si, dr);
-    Vr[s | SB] = f2add(sr, di);
-    Vi[s | SB] = f2sub(si, dr);
-  }
-}
-// 2 Y^1/2 = [[1+i, -1-i], [1+i, 1+i]]: out0 = (1+i)(a-b), out1 = (1+i)(a+b)
-template <int R, int J>
-__device__ __forceinline__ void pk_yh(float2* Vr, float2* Vi) {
-  constexpr int NS = 1 << (R - 1), SB = 1 << (J - 1);
-#pragma unroll
-  for (int s = 0; s < NS; s++) {
-    if (s & SB) continue;
-    const float2 sr = f2add(Vr[s], Vr[s | SB]), si = f2add(Vi[s], Vi[s | SB]);
-    const float2 dr = f2sub(Vr[s], Vr[s | SB]), di = f2sub(Vi[s], Vi[s | SB]);
-    Vr[s] = f2sub(dr, di);
-    Vi[s] = f2add(dr, di);
-    Vr[s | SB] = f2sub(sr, si);
-    Vi[s | SB] = f2add(sr, si);
-  }
-}
-// general 2x2 (m0 m1; m2 m3) on register bit J >= 1
-template <int R, int J>
-__device__ __forceinline__ void pk_g1(float2* Vr, float2* Vi, float2 m0, float2 m1, float2 m2, float2 m3) {
-  constexpr int NS = 1 << (R - 1), SB = 1 << (J - 1);
-  const float2 m0r = make_float2(m0.x, m0.x), m0i = make_float2(m0.y, m0.y);
-  const float2 m1r = make_float2(m1.x, m1.x), m1i = make_float2(m1.y, m1.y);
-  const float2 m2r = make_float2(m2.x, m2.x), m2i = make_float2(m2.y, m2.y);
-  const float2 m3r = make_float2(m3.x, m3.x), m3i = make_float2(m3.y, m3.y);
-  const float2 n0i = make_float2(-m0.y, -m0.y), n1i = make_float2(-m1.y, -m1.y);
-  const float2 n2i = make_float2(-m2.y, -m2.y), n3i = make_float2(-m3.y, -m3.y);
-#pragma unroll
-  for (int s = 0; s < NS; s++) {
-    if (s & SB) continue;
-    const float2 ar = Vr[s], ai = Vi[s], br = Vr[s | SB], bi = Vi[s | SB];
-    Vr[s] = f2fma(m0r, ar, f2fma(n0i, ai, f2fma(m1r, br, f2mul(n1i, bi))));
-    Vi[s] = f2fma(m0r, ai, f2fma(m0i, ar, f2fma(m1r, bi, f2mul(m1i, br))));
-    Vr[s | SB] = f2fma(m2r, ar, f2fma(n2i, ai, f2fma(m3r, br, f2mul(n3i, bi))));
-    Vi[s | SB] = f2fma(m2r, ai, f2fma(m2i, ar, f2fma(m3r, bi, f2mul(m3i, br))));
-  }
-}
-
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
-// Scalar gates through the compile-time amplitude view (any register bit,
-// used for the pair bit and for two-qubit gates that involve it).
-template <int R, int J, int I = 0>
-__device__ __forceinline__ void sc_1(float2* Vr, float2* Vi, int code, float2 m0, float2 m1, float2 m2, float2 m3) {
-  if constexpr (I < (1 << R)) {
-    if constexpr (!(I & (1 << J))) {
-      const float2 a = amp_get<I>(Vr, Vi), b = amp_get<I | (1 << J)>(Vr, Vi);
-      float2 o0, o1;
-      if (code == DOP_H) {
-        o0 = make_float2(a.x + b.x, a.y + b.y);
-        o1 = make_float2(a.x - b.x, a.y - b.y);
-      } else if (code == DOP_XH) {
-        const float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
-        o0 = make_float2(sx - dy, sy + dx);
-        o1 = make_float2(sx + dy, sy - dx);
-      } else if (code == DOP_YH) {
-        const float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
-        o0 = make_float2(dx - dy, dx + dy);
-        o1 = make_float2(sx - sy, sx + sy);
-      } else {
-        o0 = cadd(cmul(m0, a), cmul(m1, b));
-        o1 = cadd(cmul(m2, a), cmul(m3, b));
-      }
-      amp_set<I>(Vr, Vi, o0);
-      amp_set<I | (1 << J)>(Vr, Vi, o1);
-    }
-    sc_1<R, J, I + 1>(Vr, Vi, code, m0, m1, m2, m3);
+// ---- register-block gate kernels (J = register bit, compile time) --------
+template <int R, int J>
+__device__ __forceinline__ void g_h(float2* v) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    v[i] = make_float2(a.x + b.x, a.y + b.y);
+    v[i | (1 << J)] = make_float2(a.x - b.x, a.y - b.y);
   }
 }
-template <int R, int J, int I = 0>
-__device__ __forceinline__ void sc_dmul(float2* Vr, float2* Vi, float2 f0, float2 f1) {
-  if constexpr (I < (1 << R)) {
-    amp_set<I>(Vr, Vi, cmul((I & (1 << J)) ? f1 : f0, amp_get<I>(Vr, Vi)));
-    sc_dmul<R, J, I + 1>(Vr, Vi, f0, f1);
+// 2 X^1/2 = [[1+i, 1-i], [1-i, 1+i]]: out0 = s + i d, out1 = s - i d
+template <int R, int J>
+__device__ __forceinline__ void g_xh(float2* v) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
+    v[i] = make_float2(sx - dy, sy + dx);
+    v[i | (1 << J)] = make_float2(sx + dy, sy - dx);
   }
 }
-// 4x4 on register bits (A = high bit of the basis index, B = low bit)
-template <int R, int A, int B, int I = 0>
-__device__ __forceinline__ void sc_2(float2* Vr, float2* Vi, const float* m) {
-  if constexpr (I < (1 << R)) {
-    if constexpr (!(I & ((1 << A) | (1 << B)))) {
-      constexpr int i0 = I, i1 = I | (1 << B), i2 = I | (1 << A), i3 = I | (1 << A) | (1 << B);
-      const float2 x[4] = {amp_get<i0>(Vr, Vi), amp_get<i1>(Vr, Vi), amp_get<i2>(Vr, Vi), amp_get<i3>(Vr, Vi)};
-      float2 y[4];
+// 2 Y^1/2 = [[1+i, -1-i], [1+i, 1+i]]: out0 = (1+i)(a-b), out1 = (1+i)(a+b)
+template <int R, int J>
+__device__ __forceinline__ void g_yh(float2* v) {
 #pragma unroll
-      for (int r = 0; r < 4; r++) {
-        float2 acc = make_float2(0.f, 0.f);
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
+    v[i] = make_float2(dx - dy, dx + dy);
+    v[i | (1 << J)] = make_float2(sx - sy, sx + sy);
+  }
+}
+template <int R, int J>
+__device__ __forceinline__ void g_1(float2* v, float2 m0, float2 m1, float2 m2, float2 m3) {
 #pragma unroll
-        for (int c = 0; c < 4; c++)
-          acc = cadd(acc, cmul(make_float2(m[2 * (4 * r + c)], m[2 * (4 * r + c) + 1]), x[c]));
-        y[r] = acc;
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & (1 << J)) continue;
+    float2 a = v[i], b = v[i | (1 << J)];
+    v[i] = cadd(cmul(m0, a), cmul(m1, b));
+    v[i | (1 << J)] = cadd(cmul(m2, a), cmul(m3, b));
+  }
+}
+template <int R, int J>
+__device__ __forceinline__ void g_dmul(float2* v, float2 f0, float2 f1) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) v[i] = cmul((i & (1 << J)) ? f1 : f0, v[i]);
+}
+// 4x4 on register bits (A = high basis bit, B = low basis bit)
+template <int R, int A, int B>
+__device__ __forceinline__ void g_2(float2* v, const float* m) {
+#pragma unroll
+  for (int i = 0; i < (1 << R); i++) {
+    if (i & ((1 << A) | (1 << B))) continue;
+    const int i0 = i, i1 = i | (1 << B), i2 = i | (1 << A), i3 = i | (1 << A) | (1 << B);
+    float2 x[4] = {v[i0], v[i1], v[i2], v[i3]};
+    float2 y[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        float2 mm = make_float2(m[2 * (4 * r + c)], m[2 * (4 * r + c) + 1]);
+        acc = cadd(acc, cmul(mm, x[c]));
       }
-      amp_set<i0>(Vr, Vi, y[0]);
-      amp_set<i1>(Vr, Vi, y[1]);
-      amp_set<i2>(Vr, Vi, y[2]);
-      amp_set<i3>(Vr, Vi, y[3]);
+      y[r] = acc;
     }
-    sc_2<R, A, B, I + 1>(Vr, Vi, m);
+    v[i0] = y[0];
+    v[i1] = y[1];
+    v[i2] = y[2];
+    v[i3] = y[3];
   }
 }
 
 template <int R>
-__device__ __forceinline__ void dispatch_1q(int code, int a, float2* Vr, float2* Vi) {
-#define SF_CASE(J)                                                                      \
-  case J:                                                                               \
-    if constexpr (J < R) {                                                              \
-      if constexpr (J == 0) {                                                           \
-        const float2 z = make_float2(0.f, 0.f);                                         \
-        sc_1<R, 0>(Vr, Vi, code, z, z, z, z);                                           \
-      } else {                                                                          \
-        if (code == DOP_H) pk_h<R, (J > 0 ? J : 1)>(Vr, Vi);                           \
-        else if (code == DOP_XH) pk_xh<R, (J > 0 ? J : 1)>(Vr, Vi);                    \
-        else pk_yh<R, (J > 0 ? J : 1)>(Vr, Vi);                                         \
-      }                                                                                 \
-    }                                                                                   \
+__device__ __forceinline__ void dispatch_1q(int code, int a, float2* v) {
+#define SF_CASE(J)                                    \
+  case J:                                             \
+    if constexpr (J < R) {                            \
+      if (code == DOP_H) g_h<R, J>(v);                \
+      else if (code == DOP_XH) g_xh<R, J>(v);         \
+      else g_yh<R, J>(v);                             \
+    }                                                 \
     break;
   switch (a) { SF_CASE(0) SF_CASE(1) SF_CASE(2) SF_CASE(3) SF_CASE(4) }
 #undef SF_CASE
 }
 
 template <int R>
-__device__ __forceinline__ void dispatch_g1(int a, float2* Vr, float2* Vi, float2 m0, float2 m1, float2 m2, float2 m3) {
-#define SF_CASE(J)                                                   \
-  case J:                                                            \
-    if constexpr (J < R) {                                           \
-      if constexpr (J == 0) sc_1<R, 0>(Vr, Vi, DOP_G1, m0, m1, m2, m3); \
-      else pk_g1<R, (J > 0 ? J : 1)>(Vr, Vi, m0, m1, m2, m3);       \
-    }                                                                \
-    break;
-  switch (a) { SF_CASE(0) SF_CASE(1) SF_CASE(2) SF_CASE(3) SF_CASE(4) }
-#undef SF_CASE
-}
-
-template <int R>
-__device__ __forceinline__ void dispatch_dmul(int a, float2* Vr, float2* Vi, float2 f0, float2 f1) {
+__device__ __forceinline__ void dispatch_g1(int a, float2* v, float2 m0, float2 m1, float2 m2, float2 m3) {
 #define SF_CASE(J) \
   case J:          \
-    if constexpr (J < R) sc_dmul<R, J>(Vr, Vi, f0, f1); \
+    if constexpr (J < R) g_1<R, J>(v, m0, m1, m2, m3); \
     break;
   switch (a) { SF_CASE(0) SF_CASE(1) SF_CASE(2) SF_CASE(3) SF_CASE(4) }
 #undef SF_CASE
 }
 
 template <int R>
-__device__ __forceinline__ void dispatch_g2(int a, int b, float2* Vr, float2* Vi, const float* m) {
+__device__ __forceinline__ void dispatch_dmul(int a, float2* v, float2 f0, float2 f1) {
+#define SF_CASE(J) \
+  case J:          \
+    if constexpr (J < R) g_dmul<R, J>(v, f0, f1); \
+    break;
+  switch (a) { SF_CASE(0) SF_CASE(1) SF_CASE(2) SF_CASE(3) SF_CASE(4) }
+#undef SF_CASE
+}
+
+template <int R>
+__device__ __forceinline__ void dispatch_g2(int a, int b, float2* v, const float* m) {
 #define SF_C2(A, B)                                                          \
   case (A * 8 + B):                                                          \
-    if constexpr (A < R && B < R && A != B) sc_2<R, A, B>(Vr, Vi, m);       \
+    if constexpr (A < R && B < R && A != B) g_2<R, A, B>(v, m); \
     break;
 #define SF_ROW(A) SF_C2(A, 0) SF_C2(A, 1) SF_C2(A, 2) SF_C2(A, 3) SF_C2(A, 4)
   switch (a * 8 + b) { SF_ROW(0) SF_ROW(1) SF_ROW(2) SF_ROW(3) SF_ROW(4) }
@@ -261,12 +173,12 @@ __device__ __forceinline__ void dispatch_g2(int a, int b, float2* Vr, float2* Vi
 }
 
 // Phase group on a register block: the quadratic form of DevPhaseGroup,
-// evaluated in Gray-code order (one update per amplitude), then a packed
-// multiply by e^{i pi k/4} with (cos, sin, -sin) from a shared-memory table.
+// evaluated in Gray-code order (one update per amplitude), then a multiply by
+// e^{i pi k/4} from a table in shared memory.
 template <int R>
-__device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* Vr, float2* Vi, uint32_t gfix,
+__device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* v, uint32_t gfix,
                                             const uint8_t* xshift, const uint8_t* xbits, uint64_t path,
-                                            const float4* w8) {
+                                            const float2* w8) {
   int k0 = __popc(gfix & g.m1) + 2 * __popc(gfix & g.m2) + 4 * __popc(gfix & g.m4);
   for (int c = 0; c < g.nsh; c++) k0 += 4 * __popc(gfix & (gfix >> g.sh[c]) & g.shm[c]);
   int w[R];
@@ -284,25 +196,18 @@ __device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* Vr, 
       k0 += ws * (int)((gfix >> g.sel[s].pos) & 1u);
     }
   }
-  // slots in Gray-code order over register bits 1..R-1; the odd lane adds
-  // register bit 0's weight and its CZ partners among the slot's bits
-  int ke = k0;
+  int kk = k0;
+  v[0] = cmul(v[0], w8[kk & 7]);
 #pragma unroll
-  for (int q = 0; q < (1 << (R - 1)); q++) {
-    const int s = q ^ (q >> 1);  // slot (compile time)
-    if (q) {
-      const int sprev = (q - 1) ^ ((q - 1) >> 1);
-      const int jb = cctz(s ^ sprev) + 1;               // register bit flipped
-      const int rest = (s << 1) & ~(1 << jb);           // other register bits set
-      const int delta = w[jb] + 4 * __popc((uint32_t)g.czq[jb] & (uint32_t)rest);
-      ke = (s & (1 << (jb - 1))) ? ke + delta : ke - delta;
-    }
-    const int ko = ke + w[0] + 4 * __popc((uint32_t)g.czq[0] & (uint32_t)(s << 1));
-    const float4 t0 = w8[ke & 7], t1 = w8[ko & 7];
-    const float2 C = make_float2(t0.x, t1.x), S = make_float2(t0.y, t1.y), NS = make_float2(t0.z, t1.z);
-    const float2 vr = Vr[s], vi = Vi[s];
-    Vr[s] = f2fma(vr, C, f2mul(vi, NS));
-    Vi[s] = f2fma(vr, S, f2mul(vi, C));
+  for (int i = 1; i < (1 << R); i++) {
+    const int gi = i ^ (i >> 1);
+    const int prev = (i - 1) ^ ((i - 1) >> 1);
+    const int j = cctz(gi ^ prev);  // flipped bit (compile time)
+    const int rest = gi & ~(1 << j);
+    const int delta = w[j] + 4 * __popc((uint32_t)g.czq[j] & (uint32_t)rest);
+    if (gi & (1 << j)) kk += delta;
+    else kk -= delta;
+    v[gi] = cmul(v[gi], w8[kk & 7]);
   }
 }
 
@@ -409,7 +314,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 
 template <int R, bool GEN>
-__device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, const ItemGeo& g, const float4* w8,
+__device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
                                            float post_scale, int ncomp) {
   const DevPass& d = P.pass;
   const int k = d.k;
@@ -429,21 +334,15 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
       gfix |= b << st.tg[t];
     }
     const uint32_t pfix = swz(lfix);
-    float2 Vr[1 << (R - 1)], Vi[1 << (R - 1)];
+    float2 v[1 << R];
     {
       uint32_t addr = pfix;
+      v[0] = sm[addr];
 #pragma unroll
-      for (int i = 0; i < (1 << R); i++) {
-        const int gi = i ^ (i >> 1);
-        if (i) addr ^= poff[cctz(gi ^ ((i - 1) ^ ((i - 1) >> 1)))];
-        const float2 t = sm[addr];
-        if (gi & 1) {
-          Vr[gi >> 1].y = t.x;
-          Vi[gi >> 1].y = t.y;
-        } else {
-          Vr[gi >> 1].x = t.x;
-          Vi[gi >> 1].x = t.y;
-        }
+      for (int i = 1; i < (1 << R); i++) {
+        const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
+        addr ^= poff[cctz(gi ^ prev)];
+        v[gi] = sm[addr];
       }
     }
     for (int o = st.op_begin; o < st.op_end; o++) {
@@ -452,74 +351,62 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
         case DOP_H:
         case DOP_XH:
         case DOP_YH:
-          dispatch_1q<R>(op.code, op.a, Vr, Vi);
+          dispatch_1q<R>(op.code, op.a, v);
           break;
         case DOP_PHASE:
-          apply_phase<R>(P.phases[op.arg], Vr, Vi, gfix, P.xshift, P.xbits, g.path, w8);
+          apply_phase<R>(P.phases[op.arg], v, gfix, P.xshift, P.xbits, g.path, w8);
           break;
         default:
           if constexpr (GEN) {
             switch (op.code) {
-              case DOP_G1: {
-                const float* m = P.mats + 2 * op.arg;
-                dispatch_g1<R>(op.a, Vr, Vi, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
-                               make_float2(m[4], m[5]), make_float2(m[6], m[7]));
-                break;
-              }
-              case DOP_G1SEL: {
-                const int dg = digit_of(P.xshift, P.xbits, g.path, op.xi);
-                const float* m = P.mats + 2 * (op.arg + 4 * dg);
-                dispatch_g1<R>(op.a, Vr, Vi, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
-                               make_float2(m[4], m[5]), make_float2(m[6], m[7]));
-                break;
-              }
-              case DOP_G2:
-                dispatch_g2<R>(op.a, op.b, Vr, Vi, P.mats + 2 * op.arg);
-                break;
-              case DOP_DMUL: {
-                const float* m = P.mats + 2 * op.arg;
-                const float2 f0 = make_float2(m[0], m[1]), f1 = make_float2(m[2], m[3]);
-                int jr = -1;
+            case DOP_G1: {
+              const float* m = P.mats + 2 * op.arg;
+              dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                             make_float2(m[4], m[5]), make_float2(m[6], m[7]));
+              break;
+            }
+            case DOP_G1SEL: {
+              const int dg = digit_of(P.xshift, P.xbits, g.path, op.xi);
+              const float* m = P.mats + 2 * (op.arg + 4 * dg);
+              dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                             make_float2(m[4], m[5]), make_float2(m[6], m[7]));
+              break;
+            }
+            case DOP_G2:
+              dispatch_g2<R>(op.a, op.b, v, P.mats + 2 * op.arg);
+              break;
+            case DOP_DMUL: {
+              const float* m = P.mats + 2 * op.arg;
+              const float2 f0 = make_float2(m[0], m[1]), f1 = make_float2(m[2], m[3]);
+              int jr = -1;
 #pragma unroll
-                for (int j = 0; j < R; j++)
-                  if (gr[j] == op.a) jr = j;
-                if (jr >= 0) {
-                  dispatch_dmul<R>(jr, Vr, Vi, f0, f1);
-                } else {
-                  const float2 f = ((gfix >> op.a) & 1u) ? f1 : f0;
-                  const float2 fr = make_float2(f.x, f.x), fi = make_float2(f.y, f.y), nfi = make_float2(-f.y, -f.y);
+              for (int j = 0; j < R; j++)
+                if (gr[j] == op.a) jr = j;
+              if (jr >= 0) {
+                dispatch_dmul<R>(jr, v, f0, f1);
+              } else {
+                const float2 f = ((gfix >> op.a) & 1u) ? f1 : f0;
 #pragma unroll
-                  for (int q = 0; q < (1 << (R - 1)); q++) {
-                    const float2 vr = Vr[q], vi = Vi[q];
-                    Vr[q] = f2fma(fr, vr, f2mul(nfi, vi));
-                    Vi[q] = f2fma(fr, vi, f2mul(fi, vr));
-                  }
-                }
-                break;
+                for (int i = 0; i < (1 << R); i++) v[i] = cmul(f, v[i]);
               }
-              default:
+              break;
+            }
+            default:
                 break;
             }
           }
           break;
       }
     }
-    if (s == d.n_stages - 1 && post_scale != 1.0f) {
-      const float2 sc = make_float2(post_scale, post_scale);
-#pragma unroll
-      for (int q = 0; q < (1 << (R - 1)); q++) {
-        Vr[q] = f2mul(Vr[q], sc);
-        Vi[q] = f2mul(Vi[q], sc);
-      }
-    }
+    const float sc = (s == d.n_stages - 1) ? post_scale : 1.0f;
     {
       uint32_t addr = pfix;
+      sm[addr] = make_float2(v[0].x * sc, v[0].y * sc);
 #pragma unroll
-      for (int i = 0; i < (1 << R); i++) {
-        const int gi = i ^ (i >> 1);
-        if (i) addr ^= poff[cctz(gi ^ ((i - 1) ^ ((i - 1) >> 1)))];
-        const float2 t = (gi & 1) ? make_float2(Vr[gi >> 1].y, Vi[gi >> 1].y) : make_float2(Vr[gi >> 1].x, Vi[gi >> 1].x);
-        sm[addr] = t;
+      for (int i = 1; i < (1 << R); i++) {
+        const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
+        addr ^= poff[cctz(gi ^ prev)];
+        sm[addr] = make_float2(v[gi].x * sc, v[gi].y * sc);
       }
     }
     compute_bar(ncomp);
@@ -559,7 +446,7 @@ __global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ Pa
   uint64_t* full = reinterpret_cast<uint64_t*>(runoff + ((nruns + 1) & ~1));
   uint64_t* empty = full + NBUF;
   uint64_t* freeb = empty + NBUF;
-  __shared__ float4 w8[8];  // e^{i pi t/4} as (cos, sin, -sin, 0)
+  __shared__ float2 w8[8];
   __shared__ int abort_flag;
   const int tiles_log2 = d.n_free;
   const int64_t items = (int64_t)P.n_nodes << tiles_log2;
@@ -573,7 +460,7 @@ __global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ Pa
     const int t = threadIdx.x;
     float re = (t == 0) ? 1.f : (t == 2 || t == 6) ? 0.f : (t == 4) ? -1.f : (t == 1 || t == 7) ? c : -c;
     float im = (t == 2) ? 1.f : (t == 6) ? -1.f : (t == 0 || t == 4) ? 0.f : (t == 1 || t == 3) ? c : -c;
-    w8[t] = make_float4(re, im, -im, 0.f);
+    w8[t] = make_float2(re, im);
   }
   for (int rI = threadIdx.x; rI < nruns; rI += blockDim.x) {
     uint32_t hi = 0;
@@ -943,6 +830,48 @@ void launch_frugal(const double* amps, const double* u, int64_t n, double N, dou
   frugal_accept_kernel<<<(int)blocks, 256, 0, s>>>(amps, u, n, N, mp, scale, acc,
                                                     reinterpret_cast<unsigned long long*>(count));
   check(cudaGetLastError(), "frugal_accept_kernel launch");
+}
+
+// Overlap sums for the validation protocol (Appendix C): one block-level FP64
+// reduction per block, then atomics into the 4 outputs.
+__global__ void overlap_kernel(const double* a, const double* b, int64_t n, double* out) {
+  double r = 0, im = 0, na = 0, nb = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ar = a[2 * i], ai = a[2 * i + 1], br = b[2 * i], bi = b[2 * i + 1];
+    r += ar * br + ai * bi;
+    im += ar * bi - ai * br;
+    na += ar * ar + ai * ai;
+    nb += br * br + bi * bi;
+  }
+  __shared__ double red[4][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    r += __shfl_down_sync(0xffffffffu, r, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+    na += __shfl_down_sync(0xffffffffu, na, o);
+    nb += __shfl_down_sync(0xffffffffu, nb, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = r;
+    red[1][w] = im;
+    red[2][w] = na;
+    red[3][w] = nb;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += red[threadIdx.x][q];
+    atomicAdd(&out[threadIdx.x], t);
+  }
+}
+
+void launch_overlap(const double* a, const double* b, int64_t n, double* out, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  check(cudaMemsetAsync(out, 0, 4 * sizeof(double), s), "cudaMemsetAsync");
+  if (n <= 0) return;
+  int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 4);
+  overlap_kernel<<<(int)blocks, 256, 0, s>>>(a, b, n, out);
+  check(cudaGetLastError(), "overlap_kernel launch");
 }
 
 }  // namespace sf

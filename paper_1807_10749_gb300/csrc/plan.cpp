@@ -691,23 +691,9 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
         DevStage st;
         std::memset(&st, 0, sizeof(st));
         st.r = R;
-        // register bit 0 is the kernel's pair bit (its gates run unpacked):
-        // give it the register bit with the fewest non-diagonal gates
-        int pair_lb = -1, best_cnt = 1 << 30;
-        for (int lb = 0; lb < k; lb++) {
-          if (!((Sreg >> lb) & 1)) continue;
-          int cnt = 0;
-          for (const HOp* o : st_ops)
-            if (!o->diag() && (local_of[o->p0] == lb || (o->p1 >= 0 && local_of[o->p1] == lb))) cnt++;
-          if (cnt < best_cnt) {
-            best_cnt = cnt;
-            pair_lb = lb;
-          }
-        }
         int q = 0;
-        st.rbit[q++] = (int8_t)pair_lb;
         for (int lb = 0; lb < k; lb++)
-          if (((Sreg >> lb) & 1) && lb != pair_lb) st.rbit[q++] = (int8_t)lb;
+          if ((Sreg >> lb) & 1) st.rbit[q++] = (int8_t)lb;
         {
           int t = 0;
           for (int lb = 0; lb < k; lb++)

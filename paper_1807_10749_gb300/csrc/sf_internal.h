@@ -339,6 +339,7 @@ void prof_release(Plan& p);
 void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, void* stream);
 void launch_gather(const GatherLaunch& L, void* stream);
 void launch_zero(double* p, int64_t n_doubles, void* stream);
+void launch_overlap(const double* a, const double* b, int64_t n, double* out, void* stream);
 void launch_frugal(const double* amps, const double* u, int64_t n, double N, double mp, double scale,
                    uint8_t* acc, int64_t* count, void* stream);
 

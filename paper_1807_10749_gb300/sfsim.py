@@ -28,7 +28,8 @@ EXPORTED = [
     "sf_amplitudes_device", "sf_server_create", "sf_server_submit", "sf_server_wait",
     "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_plan_profile",
     "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_plan_segment_stats",
-    "sf_plan_describe", "sf_frugal_accept_device", "sf_plan_autotune", "sf_last_error",
+    "sf_plan_describe", "sf_frugal_accept_device", "sf_plan_autotune", "sf_overlap_device",
+    "sf_last_error",
 ]
 
 
@@ -99,6 +100,7 @@ def lib():
             "sf_frugal_accept_device": (i32, [P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               P, P, P]),
             "sf_plan_autotune": (i32, [P, P, P, i64, P, i64, P, P]),
+            "sf_overlap_device": (i32, [P, P, i64, P, P]),
             "sf_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -327,6 +329,22 @@ def sf_frugal_accept_device(d_amps, d_uniform, n_qubits, mprime, d_accept, d_cou
                                          d_uniform.numel(), float(2.0 ** n_qubits), float(mprime),
                                          float(prob_scale), ctypes.c_void_p(d_accept.data_ptr()),
                                          ctypes.c_void_p(d_count.data_ptr()), ctypes.c_void_p(stream.cuda_stream)))
+
+
+def sf_overlap_device(d_a, d_b, d_out, stream=None):
+    """<a|b>, <a|a>, <b|b> of two float64 (n, 2) device tensors into d_out (4,)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().sf_overlap_device(ctypes.c_void_p(d_a.data_ptr()), ctypes.c_void_p(d_b.data_ptr()),
+                                   d_a.shape[0], ctypes.c_void_p(d_out.data_ptr()),
+                                   ctypes.c_void_p(stream.cuda_stream)))
+
+
+def fidelity_estimate(sums):
+    """f_e = |<a|b>|^2 / (<a|a><b|b>) from the four sums of sf_overlap_device."""
+    re, im, na, nb = [float(v) for v in sums]
+    return (re * re + im * im) / (na * nb)
 
 
 def sf_last_error() -> str:

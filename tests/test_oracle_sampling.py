@@ -43,3 +43,27 @@ def test_acceptance_rule_and_rate_on_porter_thomas():
     assert not np.any(b & (p > M / N))
     # a planted mistake (N p / M' replaced by p / M') accepts almost nothing
     assert (u < np.minimum(1.0, p / 10)).mean() < 1e-3
+
+
+def test_validation_protocol_oracle():
+    """Appendix C: the Verifier sums a fraction of the paths, reaching a state
+    of fidelity f1 (its squared norm, here known over all 2^16 bitstrings);
+    on k = 4096 seeded bitstrings the exact Claimant's amplitudes give
+    f_e within delta of f1, while a Claimant who simulated another circuit
+    gives f_e ~ 0 and fails; identical states give 1."""
+    from oracle import paths, validation
+    c = circuit.parse(inputs.google_circuit(4, 4, 32, 5).text())
+    xs = np.arange(1 << 16, dtype=np.uint64)
+    exact = sim.sv_amplitudes(c, xs)
+    setup = sim.SFSetup(c, inputs.WORKLOADS["4x4_d10"]["side_b_mask"])
+    ids, _ = paths.select_fraction(setup.x_bits, 1 / 4, 21)
+    ver = sim.sf_amplitudes(setup, ids, xs)
+    f1 = validation.fidelity_estimate(exact, ver)
+    assert 0.1 < f1 < 0.4
+    assert abs(f1 - np.vdot(ver, ver).real) < 1e-9   # fidelity of a path-sum = its norm here
+    k = np.random.default_rng(3).choice(1 << 16, 4096, replace=False)
+    assert abs(validation.fidelity_estimate(exact, exact) - 1) < 1e-12
+    assert validation.protocol_passes(exact[k], ver[k], f1, 0.02)
+    other = sim.sv_amplitudes(circuit.parse(inputs.google_circuit(4, 4, 32, 6).text()), xs)
+    assert validation.fidelity_estimate(other[k], ver[k]) < 0.01
+    assert not validation.protocol_passes(other[k], ver[k], f1, 0.02)

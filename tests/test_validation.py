@@ -1,0 +1,95 @@
+"""Validation protocol of Appendix C on the GPU path, through the C ABI:
+sf_overlap_device against the oracle's overlap sums on the same amplitudes,
+then the protocol itself on the 30-qubit 5x6, depth 1+24+1 circuit."""
+import numpy as np
+import pytest
+
+from oracle import validation
+from paper_1807_10749_gb300 import inputs, sfsim
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1807_10749_gb300 import build
+    build.build()
+
+
+def _overlap(a, b):
+    import torch
+    da = torch.from_numpy(np.stack([a.real, a.imag], 1).copy()).cuda()
+    db = torch.from_numpy(np.stack([b.real, b.imag], 1).copy()).cuda()
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    sfsim.sf_overlap_device(da, db, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [0, 1, 255, 257, 100003])
+def test_overlap_sums_match_oracle(n):
+    rng = np.random.default_rng(n + 1)
+    a = rng.normal(size=n) + 1j * rng.normal(size=n)
+    b = rng.normal(size=n) + 1j * rng.normal(size=n)
+    got = _overlap(a, b)
+    want = np.array(validation.overlap_sums(a, b)) if n else np.zeros(4)
+    # FP64 sums in another order: relative rounding ~ n * 2^-53
+    assert np.all(np.abs(got - want) <= 1e-12 * (np.abs(a).sum() * np.abs(b).sum() / max(n, 1) + n))
+
+
+@pytest.fixture(scope="module")
+def c2():
+    w = inputs.WORKLOADS["5x6_d24"]
+    plan = sfsim.Plan(inputs.workload_circuit("5x6_d24").text(), side_b_mask=w["side_b_mask"])
+    bits = inputs.random_bitstrings(30, w["n_bitstrings"], 77)   # the Verifier's seeded indices
+    exact, _ = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=1.0))
+    yield plan, bits, exact
+    plan.close()
+
+
+@pytest.mark.parametrize("f", [1 / 4, 1 / 16, 1 / 64])
+def test_fidelity_estimate_tracks_f_actual(c2, f):
+    """The exact Claimant against a Verifier at fidelity f: f_e within 10% of
+    f_actual, and within 0.02 of the Verifier's own estimate 2^n E|v|^2."""
+    plan, bits, exact = c2
+    ver, f_actual = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=f, seed=5))
+    sums = _overlap(exact, ver)
+    np.testing.assert_allclose(sums, validation.overlap_sums(exact, ver), rtol=1e-10)
+    fe = sfsim.fidelity_estimate(sums)
+    f1 = 2.0 ** 30 * np.mean(np.abs(ver) ** 2)
+    assert abs(fe - f_actual) <= 0.1 * f_actual, (fe, f_actual)
+    assert abs(fe - f1) <= 0.02 + 0.1 * f1, (fe, f1)
+
+
+def test_protocol_pass_and_fail(c2):
+    plan, bits, exact = c2
+    ver, _ = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=1 / 8, seed=5))
+    f1 = 2.0 ** 30 * np.mean(np.abs(ver) ** 2)
+    delta = 0.03
+    assert validation.protocol_passes(exact, ver, f1, delta)
+    assert abs(sfsim.fidelity_estimate(_overlap(exact, ver)) - f1) <= delta
+    # a Claimant that simulated another circuit of the family fails
+    spec = inputs.google_circuit(5, 6, 24, 1234)
+    wrong = sfsim.Plan(spec.text(), side_b_mask=inputs.WORKLOADS["5x6_d24"]["side_b_mask"])
+    bad, _ = wrong.amplitudes(bits, sfsim.selection("fraction", fidelity=1.0))
+    fe_bad = sfsim.fidelity_estimate(_overlap(bad, ver))
+    assert fe_bad < 0.01 and abs(fe_bad - f1) > delta
+    wrong.close()
+
+
+def test_independent_approximations_overlap_f1_times_f(c2):
+    """Two independent path subsets of fidelities f1 and f: their estimated
+    fidelity is f1*f on average over the seeds (Appendix C)."""
+    plan, bits, exact = c2
+    got, want = [], []
+    for s in range(8):
+        v, _ = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=1 / 4, seed=100 + s))
+        w, _ = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=1 / 2, seed=200 + s))
+        f1 = sfsim.fidelity_estimate(_overlap(exact, v))
+        f = sfsim.fidelity_estimate(_overlap(exact, w))
+        got.append(sfsim.fidelity_estimate(_overlap(v, w)))
+        want.append(f1 * f)
+    print("overlap per seed", np.round(got, 4), "f1*f", np.round(want, 4))
+    assert abs(np.mean(got) - np.mean(want)) <= 0.3 * np.mean(want)
