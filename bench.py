@@ -104,9 +104,11 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources the pass kernels are built from."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1807_10749_gb300", "csrc", "kernels.cu"), "rb") as fh:
-        h.update(fh.read())
+    for f in ("kernels.cu", "pass_common.cuh", "dev_types.h", "jit.cpp"):
+        with open(os.path.join(ROOT, "paper_1807_10749_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -117,7 +119,7 @@ def ncu_traffic(n_nodes_bytes_per_launch):
     try:
         with open(path) as fh:
             d = json.load(fh)
-        if d.get("kernels_cu_sha256_16") != kernel_source_hash():
+        if d.get("pass_sources_sha256_16") != kernel_source_hash():
             return None
         return float(d["dram_bytes_per_launch"])
     except Exception:
@@ -287,6 +289,8 @@ def main():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--fuse-bits", type=int, default=0)
     ap.add_argument("--run-bits", type=int, default=0)
+    ap.add_argument("--jit", type=int, default=1, choices=[0, 1],
+                    help="1: per-pass specialised kernels compiled at plan time; 0: the generic pass kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -315,8 +319,10 @@ def main():
     nq = w["rows"] * w["cols"]
     bits = inputs.random_bitstrings(nq, args.bitstrings, w["bitstring_seed"])
     mode = sfsim.SF_EXEC_PLAIN if args.exec_mode == "plain" else sfsim.SF_EXEC_BATCHED
+    t_plan = time.perf_counter()
     plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode, tile_bits=args.tile_bits,
-                      fuse_bits=args.fuse_bits, run_bits=args.run_bits)
+                      fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit)
+    t_plan = time.perf_counter() - t_plan
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
     n_steps_total = args.warmup + args.steps
@@ -382,7 +388,8 @@ def main():
         # the plain form: the same kernels, one path at a time from the prefix
         # checkpoint (no shared levels below it, no folded last level)
         pplan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN,
-                           tile_bits=args.tile_bits, fuse_bits=args.fuse_bits, run_bits=args.run_bits)
+                           tile_bits=args.tile_bits, fuse_bits=args.fuse_bits, run_bits=args.run_bits,
+                           jit=args.jit)
         pws = torch.empty(sfsim.sf_workspace_size(pplan.handle, len(bits), sels[0]), dtype=torch.uint8,
                           device=f"cuda:{dev}")
         sub = [sfsim.selection("range", first=int(prefixes[args.warmup]), count=16)]
@@ -418,9 +425,12 @@ def main():
             "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
                                               "tile_bits": args.tile_bits or 13, "fuse_bits": args.fuse_bits or 5,
                                               "run_bits": args.run_bits or 3,
+                                              "pass_kernels": "specialised" if args.jit else "generic",
+                                              "plan_seconds": t_plan,
                                               "paths_selected": n_sel, "parallelism": f"paths x{world}",
                                               "wall_s": wall}),
-            "roofline": {"kernel": "pass_kernel (fused tile pass)", "bound": "hbm",
+            "roofline": {"kernel": ("sf_pass_spec (per-pass specialised fused tile pass)" if args.jit
+                                    else "pass_kernel (generic fused tile pass)"), "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "peak_kind": peak_kind,
                          "traffic": traffic,

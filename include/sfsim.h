@@ -106,7 +106,10 @@ typedef struct {
   int32_t batch_paths;       /* max leaf groups per launch, 0 = from budget */
   int32_t run_bits;          /* log2 contiguous amplitudes per copy run (the
                                 index bits every pass keeps active), 0 = 3 */
-  int32_t reserved[6];
+  int32_t jit;              /* 1 = compile every pass of the plan into a kernel of
+                               its own at plan time (NVRTC; SF_EUNSUPPORTED where
+                               NVRTC is missing), 0 = the generic pass kernel */
+  int32_t reserved[5];
 } sf_plan_opts;
 
 SF_API void sf_plan_opts_default(sf_plan_opts* o);

@@ -22,7 +22,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
 
 
 def _headers_mtime():
-    hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     return max(os.path.getmtime(h) for h in hs)
 
 
@@ -42,16 +42,36 @@ def _compile(src, hm, verbose):
     return obj
 
 
+def _embed_jit_sources():
+    """The specialised pass kernels are compiled at run time from the text of
+    dev_types.h and pass_common.cuh; embed both in the library."""
+    out = os.path.join(BUILD, "jit_sources.cpp")
+    ins = [os.path.join(CSRC, "dev_types.h"), os.path.join(CSRC, "pass_common.cuh")]
+    if os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(f) for f in ins):
+        return out
+    parts = ["namespace sf {"]
+    for name, f in (("kJitDevTypes", ins[0]), ("kJitPassCommon", ins[1])):
+        text = open(f).read()
+        assert ")SFJIT" not in text
+        parts.append(f'extern const char* const {name};\nconst char* const {name} = R"SFJIT({text})SFJIT";')
+    parts.append("}  // namespace sf\n")
+    with open(out + ".tmp", "w") as fh:
+        fh.write("\n".join(parts))
+    os.replace(out + ".tmp", out)
+    return out
+
+
 def build(verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    srcs.append(_embed_jit_sources())
     hm = _headers_mtime()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, hm, verbose), srcs))
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
-    cmd = [NVCC] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lpthread"]
+    cmd = [NVCC] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs + ["-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -150,7 +150,16 @@ int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out)
     o.defer_last_level = 0;
     o.batch_paths = 1;
   }
+  if (o.jit != 0 && o.jit != 1) sf::fail(SF_EINVAL, "jit must be 0 or 1");
   sf::Plan* p = sf::plan_create(c->c, o);
+  if (o.jit) {
+    try {
+      sf::jit_prepare(*p);
+    } catch (...) {
+      sf::plan_destroy(p);
+      throw;
+    }
+  }
   sf_plan* h = new sf_plan();
   h->p = p;
   *out = h;

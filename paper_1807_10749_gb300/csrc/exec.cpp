@@ -176,7 +176,8 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
       }
       void* e1 = nullptr;
       if (prof) prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes), st, &e1);
-      launch_pass(*L, tiles, plan.fuse_bits, plan.tile_bits, st);
+      if (pp.jit_id >= 0) launch_pass_jit(*L, tiles, plan.jit_entries[pp.jit_id], st);
+      else launch_pass(*L, tiles, plan.fuse_bits, plan.tile_bits, st);
       if (prof) prof_end(plan, e1, st);
     }
   }

@@ -1,0 +1,457 @@
+// Run-time specialised pass kernels.
+//
+// The generic pass kernel reads every stage, op and phase group of a pass
+// from its launch record and dispatches on them per thread. A plan is fixed
+// once it is made, so each of its passes can instead be compiled into a
+// kernel of its own: the same warp-specialised pipeline (pass_common.cuh),
+// with the stage program emitted as straight-line code. Register bits,
+// shared-memory offsets, gate kinds and matrices, and the plan-static part of
+// every phase group (the one-qubit phase weights and the CZs between register
+// bits: the quadratic form k(idx) of Section 2, mod 8) become constants, so a
+// phase costs nothing on most amplitudes. The per-thread part of a phase group
+// (terms in the thread's fixed index bits, the e^{i pi k0/4} of
+// DevPhaseGroup) is a scalar on the thread's whole register block; it is
+// summed over the stage and applied once before the stage stores.
+//
+// Compilation uses NVRTC, opened with dlopen so that the library loads where
+// it is absent (a plan that asks for these kernels then fails with
+// SF_EUNSUPPORTED). Binaries are cached per process by source text, and loaded
+// with the runtime's library API on first launch.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <thread>
+
+#include "sf_internal.h"
+
+namespace sf {
+
+extern const char* const kJitDevTypes;    // text of dev_types.h
+extern const char* const kJitPassCommon;  // text of pass_common.cuh
+
+namespace {
+
+// ------------------------------------------------------------------ NVRTC
+typedef int nvrtcResult;
+typedef struct _nvrtcProgram* nvrtcProgram;
+
+struct Nvrtc {
+  nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*, const char* const*);
+  nvrtcResult (*compile)(nvrtcProgram, int, const char* const*);
+  nvrtcResult (*log_size)(nvrtcProgram, size_t*);
+  nvrtcResult (*log)(nvrtcProgram, char*);
+  nvrtcResult (*cubin_size)(nvrtcProgram, size_t*);
+  nvrtcResult (*cubin)(nvrtcProgram, char*);
+  nvrtcResult (*destroy)(nvrtcProgram*);
+  bool ok = false;
+  std::string why;
+};
+
+const Nvrtc& nvrtc() {
+  static Nvrtc n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* env = std::getenv("SF_NVRTC");
+    const char* names[] = {env, "libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/targets/sbsa-linux/lib/libnvrtc.so.13",
+                           "/usr/local/cuda/targets/x86_64-linux/lib/libnvrtc.so.13"};
+    void* h = nullptr;
+    for (const char* nm : names)
+      if (nm && (h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) {
+      n.why = "NVRTC (libnvrtc.so.13) not found";
+      return;
+    }
+    auto sym = [&](const char* s) { return dlsym(h, s); };
+    n.create = (decltype(n.create))sym("nvrtcCreateProgram");
+    n.compile = (decltype(n.compile))sym("nvrtcCompileProgram");
+    n.log_size = (decltype(n.log_size))sym("nvrtcGetProgramLogSize");
+    n.log = (decltype(n.log))sym("nvrtcGetProgramLog");
+    n.cubin_size = (decltype(n.cubin_size))sym("nvrtcGetCUBINSize");
+    n.cubin = (decltype(n.cubin))sym("nvrtcGetCUBIN");
+    n.destroy = (decltype(n.destroy))sym("nvrtcDestroyProgram");
+    n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+    if (!n.ok) n.why = "NVRTC entry points missing";
+  });
+  return n;
+}
+
+// ------------------------------------------------------- code generation
+std::string flit(float f) {
+  if (!std::isfinite(f)) fail(SF_EINVAL, "internal: non-finite gate entry");
+  char b[48];
+  std::snprintf(b, sizeof b, "%.9ef", (double)f);
+  return b;
+}
+
+std::string f2lit(const std::vector<float>& m, int i) {  // float2 at float index 2i
+  return "make_float2(" + flit(m[2 * i]) + ", " + flit(m[2 * i + 1]) + ")";
+}
+
+// thread-index bits t -> bit positions pos[t], grouped into shifted fields
+std::string deposit(const int8_t* pos, int nbits) {
+  std::string e;
+  int t = 0;
+  while (t < nbits) {
+    int len = 1;
+    while (t + len < nbits && pos[t + len] == pos[t] + len) len++;
+    char b[96];
+    std::snprintf(b, sizeof b, "(((tid >> %d) & 0x%xu) << %d)", t, (1u << len) - 1, pos[t]);
+    if (!e.empty()) e += " | ";
+    e += b;
+    t += len;
+  }
+  return e.empty() ? "0u" : e;
+}
+
+// One pass as a stage program: struct `name`_prog in namespace sf and an
+// extern "C" kernel `name`.
+std::string gen_pass(const PassPlan& pp, const std::string& name) {
+  const DevPass& d = pp.dev;
+  const int R = d.R, k = d.k, NR = 1 << R;
+  std::ostringstream o;
+  o << "namespace sf {\nstruct " << name << "_prog {\n"
+    << "static __device__ __forceinline__ void run(const PassLaunch& P, float2* sm, const ItemGeo& g, "
+       "const float2* w8, int ncomp) {\n"
+    << "const uint32_t tid = threadIdx.x;\n(void)P; (void)g; (void)w8;\n";
+  for (int s = 0; s < d.n_stages; s++) {
+    const DevStage& st = pp.stages[s];
+    if (st.r != R) fail(SF_EINVAL, "internal: stage width differs from the pass");
+    uint32_t C[32];
+    int gr[MAX_R];
+    for (int i = 0; i < NR; i++) {
+      uint32_t c = 0;
+      for (int j = 0; j < R; j++)
+        if ((i >> j) & 1) c ^= swz(1u << st.rbit[j]);
+      C[i] = c;
+    }
+    for (int j = 0; j < R; j++) gr[j] = d.gpos[st.rbit[j]];
+    o << "{ // stage " << s << "\n";
+    o << "const uint32_t pf = swz(" << deposit(st.tpos, k - R) << ");\n";
+    o << "const uint32_t gfix = g.base | " << deposit(st.tg, k - R) << ";\n(void)gfix;\n";
+    o << "float2 v[" << NR << "];\n";
+    for (int i = 0; i < NR; i++) o << "v[" << i << "] = sm[pf ^ " << C[i] << "u];\n";
+    bool kst = false;  // per-thread phase accumulated over the stage
+    o << "int kst = 0;\n";
+    for (int oi = st.op_begin; oi < st.op_end; oi++) {
+      const DevOp& op = pp.ops[oi];
+      switch (op.code) {
+        case DOP_H:
+          o << "g_h<" << R << ", " << op.a << ">(v);\n";
+          break;
+        case DOP_XH:
+          o << "g_xh<" << R << ", " << op.a << ">(v);\n";
+          break;
+        case DOP_YH:
+          o << "g_yh<" << R << ", " << op.a << ">(v);\n";
+          break;
+        case DOP_G1:
+          o << "g_1<" << R << ", " << op.a << ">(v, " << f2lit(pp.mats, op.arg) << ", "
+            << f2lit(pp.mats, op.arg + 1) << ", " << f2lit(pp.mats, op.arg + 2) << ", "
+            << f2lit(pp.mats, op.arg + 3) << ");\n";
+          break;
+        case DOP_G1SEL:
+          o << "{ const int dg = digit_of(P.xshift, P.xbits, g.path, " << op.xi << ");\n"
+            << "const float* m = P.mats + 2 * (" << op.arg << " + 4 * dg);\n"
+            << "g_1<" << R << ", " << op.a
+            << ">(v, make_float2(m[0], m[1]), make_float2(m[2], m[3]), make_float2(m[4], m[5]), "
+               "make_float2(m[6], m[7])); }\n";
+          break;
+        case DOP_G2:
+          o << "g_2<" << R << ", " << op.a << ", " << op.b << ">(v, P.mats + " << 2 * op.arg << ");\n";
+          break;
+        case DOP_DMUL: {
+          int jr = -1;
+          for (int j = 0; j < R; j++)
+            if (gr[j] == op.a) jr = j;
+          if (jr >= 0) {
+            o << "g_dmul<" << R << ", " << jr << ">(v, " << f2lit(pp.mats, op.arg) << ", "
+              << f2lit(pp.mats, op.arg + 1) << ");\n";
+          } else {
+            o << "{ const float2 f = ((gfix >> " << op.a << ") & 1u) ? " << f2lit(pp.mats, op.arg + 1) << " : "
+              << f2lit(pp.mats, op.arg) << ";\n#pragma unroll\nfor (int i = 0; i < " << NR
+              << "; i++) v[i] = cmul(f, v[i]); }\n";
+          }
+          break;
+        }
+        case DOP_PHASE: {
+          const DevPhaseGroup& G = pp.phases[op.arg];
+          // plan-static part: weights and CZs among register bits
+          for (int j = 0; j < R; j++)
+            for (int l = 0; l < R; l++)
+              if (((G.czq[j] >> l) & 1) != ((G.czq[l] >> j) & 1))
+                fail(SF_EINVAL, "internal: asymmetric CZ partners in a phase group");
+          o << "{ // phase group " << op.arg << "\n";
+          for (int i = 0; i < NR; i++) {
+            int ku = 0;
+            for (int j = 0; j < R; j++)
+              if ((i >> j) & 1) {
+                ku += G.wstat[j];
+                for (int l = j + 1; l < R; l++)
+                  if (((i >> l) & 1) && ((G.czq[j] >> l) & 1)) ku += 4;
+              }
+            ku &= 7;
+            if (ku) o << "v[" << i << "] = omega_mul<" << ku << ">(v[" << i << "]);\n";
+          }
+          // per-thread scalar part (fixed index bits), summed over the stage
+          auto kadd = [&](const std::string& e) {
+            o << "kst += " << e << ";\n";
+            kst = true;
+          };
+          char b[160];
+          if (G.m1) {
+            std::snprintf(b, sizeof b, "__popc(gfix & 0x%xu)", G.m1);
+            kadd(b);
+          }
+          if (G.m2) {
+            std::snprintf(b, sizeof b, "2 * __popc(gfix & 0x%xu)", G.m2);
+            kadd(b);
+          }
+          if (G.m4) {
+            std::snprintf(b, sizeof b, "4 * __popc(gfix & 0x%xu)", G.m4);
+            kadd(b);
+          }
+          for (int c = 0; c < G.nsh; c++) {
+            std::snprintf(b, sizeof b, "4 * __popc(gfix & (gfix >> %d) & 0x%xu)", G.sh[c], G.shm[c]);
+            kadd(b);
+          }
+          // per-thread / per-path weights of register bits
+          std::string wr[MAX_R];
+          bool sign_only[MAX_R];
+          for (int j = 0; j < R; j++) {
+            sign_only[j] = true;
+            if (G.czf[j]) {
+              std::snprintf(b, sizeof b, "4 * __popc(gfix & 0x%xu)", G.czf[j]);
+              wr[j] = b;
+            }
+          }
+          for (int si = 0; si < G.nsel; si++) {
+            const auto& e = G.sel[si];
+            std::string dg = e.xi >= 0 ? "digit_of(P.xshift, P.xbits, g.path, " + std::to_string(e.xi) + ")" : "0";
+            std::snprintf(b, sizeof b, "(int)(0x%xu >> (8 * %s) & 0xffu)",
+                          (uint32_t)e.w[0] | (uint32_t)e.w[1] << 8 | (uint32_t)e.w[2] << 16 | (uint32_t)e.w[3] << 24,
+                          dg.c_str());
+            if (e.reg >= 0) {
+              if (!wr[e.reg].empty()) wr[e.reg] += " + ";
+              wr[e.reg] += b;
+              for (int dd = 0; dd < 4; dd++)
+                if (e.w[dd] & 3) sign_only[e.reg] = false;
+            } else {
+              kadd(std::string(b) + " * (int)((gfix >> " + std::to_string(e.pos) + ") & 1u)");
+            }
+          }
+          for (int j = 0; j < R; j++) {
+            if (wr[j].empty()) continue;
+            o << "{ const int w = " << wr[j] << ";\n";
+            if (sign_only[j]) {
+              o << "const float sg = (w & 4) ? -1.f : 1.f;\n";
+              for (int i = 0; i < NR; i++)
+                if ((i >> j) & 1) o << "v[" << i << "].x *= sg; v[" << i << "].y *= sg;\n";
+            } else {
+              o << "const float2 f = w8[w & 7];\n";
+              for (int i = 0; i < NR; i++)
+                if ((i >> j) & 1) o << "v[" << i << "] = cmul(v[" << i << "], f);\n";
+            }
+            o << "}\n";
+          }
+          o << "}\n";
+          break;
+        }
+        default:
+          fail(SF_EINVAL, "internal: op code without a specialised form");
+      }
+    }
+    const bool last = s == d.n_stages - 1;
+    const bool scale = last && d.post_scale != 1.0f;
+    if (kst) {
+      o << "{ float2 f = w8[kst & 7];\n";
+      if (scale) o << "f.x *= " << flit(d.post_scale) << "; f.y *= " << flit(d.post_scale) << ";\n";
+      o << "#pragma unroll\nfor (int i = 0; i < " << NR << "; i++) v[i] = cmul(v[i], f); }\n";
+    } else if (scale) {
+      o << "#pragma unroll\nfor (int i = 0; i < " << NR << "; i++) { v[i].x *= " << flit(d.post_scale)
+        << "; v[i].y *= " << flit(d.post_scale) << "; }\n";
+    }
+    o << "(void)kst;\n";
+    for (int i = 0; i < NR; i++) o << "sm[pf ^ " << C[i] << "u] = v[" << i << "];\n";
+    o << "compute_bar(ncomp);\n}\n";
+  }
+  o << "}\n};\n}  // namespace sf\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(320, 1) " << name
+    << "(const __grid_constant__ sf::PassLaunch P) {\n  sf::pass_body<" << R << ", sf::" << name
+    << "_prog>(P);\n}\n";
+  return o.str();
+}
+
+std::string layout_asserts() {
+  std::ostringstream o;
+  auto sz = [&](const char* t, size_t n) {
+    o << "static_assert(sizeof(sf::" << t << ") == " << n << ", \"layout of " << t << "\");\n";
+  };
+  sz("PassLaunch", sizeof(PassLaunch));
+  sz("DevPass", sizeof(DevPass));
+  sz("DevStage", sizeof(DevStage));
+  sz("DevOp", sizeof(DevOp));
+  sz("DevPhaseGroup", sizeof(DevPhaseGroup));
+  sz("PassNode", sizeof(PassNode));
+  return o.str();
+}
+
+// -------------------------------------------------------- compiled cache
+struct Entry {
+  std::string src;
+  std::string cubin;
+  std::string err;
+  bool compiled = false;
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+  size_t smem_set = 0;
+  int per_sm = 0;
+};
+
+std::mutex g_mu;
+std::map<std::string, std::unique_ptr<Entry>>& cache() {
+  static std::map<std::string, std::unique_ptr<Entry>> c;
+  return c;
+}
+
+const char* kKernelName = "sf_pass_spec";
+
+void compile_entry(Entry* e) {
+  const Nvrtc& n = nvrtc();
+  const std::string full = "#include \"dev_types.h\"\n#include \"pass_common.cuh\"\n" + layout_asserts() + e->src;
+  const char* hdrs[] = {kJitDevTypes, kJitPassCommon};
+  const char* hnames[] = {"dev_types.h", "pass_common.cuh"};
+  nvrtcProgram prog = nullptr;
+  if (n.create(&prog, full.c_str(), "sf_pass_spec.cu", 2, hdrs, hnames) != 0) {
+    e->err = "nvrtcCreateProgram failed";
+    e->compiled = true;
+    return;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG"};
+  const nvrtcResult rc = n.compile(prog, 4, opts);
+  if (rc != 0) {
+    size_t ls = 0;
+    n.log_size(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) n.log(prog, &log[0]);
+    e->err = "NVRTC compile failed: " + log.substr(0, 2000);
+  } else {
+    size_t cs = 0;
+    n.cubin_size(prog, &cs);
+    e->cubin.assign(cs, '\0');
+    n.cubin(prog, &e->cubin[0]);
+  }
+  n.destroy(&prog);
+  e->compiled = true;
+}
+
+}  // namespace
+
+// Compile (or find in the cache) a specialised kernel for every pass of the
+// plan; passes get jit_id indexes into p.jit_entries.
+void jit_prepare(Plan& p) {
+  const Nvrtc& n = nvrtc();
+  if (!n.ok) fail(SF_EUNSUPPORTED, "run-time specialised kernels need NVRTC: " + n.why);
+  std::vector<PassPlan*> all;
+  for (HalfPlan* h : {&p.A, &p.B}) {
+    for (auto& s : h->seg)
+      for (auto& pp : s.passes) all.push_back(&pp);
+    for (auto& pp : h->last_deferred.passes) all.push_back(&pp);
+  }
+  std::vector<Entry*> todo;
+  p.jit_entries.clear();
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (PassPlan* pp : all) {
+      std::string src = gen_pass(*pp, kKernelName);
+      auto& slot = cache()[src];
+      if (!slot) {
+        slot = std::make_unique<Entry>();
+        slot->src = src;
+        todo.push_back(slot.get());
+      }
+      pp->jit_id = (int)p.jit_entries.size();
+      p.jit_entries.push_back(slot.get());
+    }
+  }
+  // compile the new ones in parallel (NVRTC programs are independent)
+  unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (const char* e = std::getenv("SF_JIT_THREADS")) hw = std::max(1, std::atoi(e));
+  std::vector<std::thread> th;
+  std::mutex qmu;
+  size_t next = 0;
+  for (unsigned t = 0; t < std::min<size_t>(hw, todo.size()); t++)
+    th.emplace_back([&] {
+      while (true) {
+        size_t i;
+        {
+          std::lock_guard<std::mutex> lk(qmu);
+          if (next >= todo.size()) return;
+          i = next++;
+        }
+        compile_entry(todo[i]);
+      }
+    });
+  for (auto& t : th) t.join();
+  for (void* v : p.jit_entries) {
+    Entry* e = static_cast<Entry*>(v);
+    if (!e->err.empty()) fail(SF_EINVAL, "internal: specialised pass kernel: " + e->err);
+  }
+}
+
+std::string jit_source(const PassPlan& pp) { return gen_pass(pp, kKernelName); }
+
+// Launch a pass with its specialised kernel; same launch shape as the
+// generic kernel.
+void launch_pass_jit(const PassLaunch& L, int tiles, void* entry, void* stream) {
+  Entry* e = static_cast<Entry*>(entry);
+  const int tile_k = L.pass.k, R = L.pass.R;
+  const int nact = 1 << (tile_k - R);
+  const int threads = ((nact + 31) / 32) * 32 + 64;
+  const int nruns = 1 << (tile_k - L.pass.L);
+  const size_t smem = 3 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 9 * 8;
+  int nb;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!e->kern) {
+      cudaError_t rc = cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(rc));
+      rc = cudaLibraryGetKernel(&e->kern, e->lib, kKernelName);
+      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(rc));
+    }
+    if (smem > e->smem_set) {
+      cudaError_t rc = cudaFuncSetAttribute((const void*)e->kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem);
+      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(rc));
+      e->smem_set = smem;
+      e->per_sm = 0;
+    }
+    if (!e->per_sm) {
+      int v = 0;
+      cudaError_t rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, (const void*)e->kern, threads, smem);
+      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaOccupancy: ") + cudaGetErrorString(rc));
+      e->per_sm = v > 0 ? v : 1;
+    }
+    nb = e->per_sm;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t items = (int64_t)tiles * L.n_nodes;
+  const int64_t grid = std::min<int64_t>(items, (int64_t)sms * nb);
+  if (grid < 1) return;
+  void* args[] = {const_cast<PassLaunch*>(&L)};
+  cudaError_t rc = cudaLaunchKernel((const void*)e->kern, dim3((unsigned)grid), dim3((unsigned)threads), args, smem,
+                                    (cudaStream_t)stream);
+  if (rc != cudaSuccess) fail(SF_ECUDA, std::string("specialised pass kernel launch: ") + cudaGetErrorString(rc));
+}
+
+}  // namespace sf

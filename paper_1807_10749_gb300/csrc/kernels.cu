@@ -25,106 +25,11 @@
 #include <mutex>
 
 #include "sf_internal.h"
+#include "pass_common.cuh"
 
 namespace sf {
 
 namespace {
-
-__device__ __forceinline__ int digit_of(const uint8_t* xshift, const uint8_t* xbits, uint64_t path,
-                                        int xi) {
-  return (int)((path >> xshift[xi]) & ((1u << xbits[xi]) - 1u));
-}
-
-// count of trailing zeros, folded at compile time for unrolled loop indices
-__host__ __device__ constexpr int cctz(int v) {
-  int r = 0;
-  while (v && !(v & 1)) {
-    v >>= 1;
-    r++;
-  }
-  return r;
-}
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-
-// ---- register-block gate kernels (J = register bit, compile time) --------
-template <int R, int J>
-__device__ __forceinline__ void g_h(float2* v) {
-#pragma unroll
-  for (int i = 0; i < (1 << R); i++) {
-    if (i & (1 << J)) continue;
-    float2 a = v[i], b = v[i | (1 << J)];
-    v[i] = make_float2(a.x + b.x, a.y + b.y);
-    v[i | (1 << J)] = make_float2(a.x - b.x, a.y - b.y);
-  }
-}
-// 2 X^1/2 = [[1+i, 1-i], [1-i, 1+i]]: out0 = s + i d, out1 = s - i d
-template <int R, int J>
-__device__ __forceinline__ void g_xh(float2* v) {
-#pragma unroll
-  for (int i = 0; i < (1 << R); i++) {
-    if (i & (1 << J)) continue;
-    float2 a = v[i], b = v[i | (1 << J)];
-    float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
-    v[i] = make_float2(sx - dy, sy + dx);
-    v[i | (1 << J)] = make_float2(sx + dy, sy - dx);
-  }
-}
-// 2 Y^1/2 = [[1+i, -1-i], [1+i, 1+i]]: out0 = (1+i)(a-b), out1 = (1+i)(a+b)
-template <int R, int J>
-__device__ __forceinline__ void g_yh(float2* v) {
-#pragma unroll
-  for (int i = 0; i < (1 << R); i++) {
-    if (i & (1 << J)) continue;
-    float2 a = v[i], b = v[i | (1 << J)];
-    float sx = a.x + b.x, sy = a.y + b.y, dx = a.x - b.x, dy = a.y - b.y;
-    v[i] = make_float2(dx - dy, dx + dy);
-    v[i | (1 << J)] = make_float2(sx - sy, sx + sy);
-  }
-}
-template <int R, int J>
-__device__ __forceinline__ void g_1(float2* v, float2 m0, float2 m1, float2 m2, float2 m3) {
-#pragma unroll
-  for (int i = 0; i < (1 << R); i++) {
-    if (i & (1 << J)) continue;
-    float2 a = v[i], b = v[i | (1 << J)];
-    v[i] = cadd(cmul(m0, a), cmul(m1, b));
-    v[i | (1 << J)] = cadd(cmul(m2, a), cmul(m3, b));
-  }
-}
-template <int R, int J>
-__device__ __forceinline__ void g_dmul(float2* v, float2 f0, float2 f1) {
-#pragma unroll
-  for (int i = 0; i < (1 << R); i++) v[i] = cmul((i & (1 << J)) ? f1 : f0, v[i]);
-}
-// 4x4 on register bits (A = high basis bit, B = low basis bit)
-template <int R, int A, int B>
-__device__ __forceinline__ void g_2(float2* v, const float* m) {
-#pragma unroll
-  for (int i = 0; i < (1 << R); i++) {
-    if (i & ((1 << A) | (1 << B))) continue;
-    const int i0 = i, i1 = i | (1 << B), i2 = i | (1 << A), i3 = i | (1 << A) | (1 << B);
-    float2 x[4] = {v[i0], v[i1], v[i2], v[i3]};
-    float2 y[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) {
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int c = 0; c < 4; c++) {
-        float2 mm = make_float2(m[2 * (4 * r + c)], m[2 * (4 * r + c) + 1]);
-        acc = cadd(acc, cmul(mm, x[c]));
-      }
-      y[r] = acc;
-    }
-    v[i0] = y[0];
-    v[i1] = y[1];
-    v[i2] = y[2];
-    v[i3] = y[3];
-  }
-}
 
 template <int R>
 __device__ __forceinline__ void dispatch_1q(int code, int a, float2* v) {
@@ -211,111 +116,12 @@ __device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* v, u
   }
 }
 
-__device__ __forceinline__ uint32_t pin_val(const DevPin& p, const uint8_t* xshift, const uint8_t* xbits,
-                                            uint64_t path) {
-  return p.xi < 0 ? p.v[0] : p.v[digit_of(xshift, xbits, path, p.xi)];
-}
-
 }  // namespace
-
-// ---- mbarriers and asynchronous copies (inline PTX) ------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-// Wait for phase `parity` of the barrier, giving up after ~2^31 cycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > (1ll << 31)) return false;
-  }
-}
-
-// Shared-memory layout of a tile: element e lives at swz(e), a linear XOR
-// swizzle that folds index bits 4..12 into bits 1..3. It keeps 16-byte
-// chunks (element pairs) intact for the copy warps and, being linear,
-// swz(a ^ b) = swz(a) ^ swz(b), so register stages still step addresses with
-// one XOR per amplitude; it spreads the stages' strided accesses over the
-// shared-memory banks (at most two wavefronts per half-warp).
-__device__ __forceinline__ uint32_t swz(uint32_t e) {
-  const uint32_t x = e >> 4;
-  return e ^ (((x ^ (x >> 3) ^ (x >> 6)) & 7u) << 1);
-}
-
-// Per-item geometry: tile base index and pin masks (tile-local and run-level).
-struct ItemGeo {
-  uint32_t base;                 // global index bits of the tile (inactive bits)
-  uint32_t lin_m, lin_v;         // input pins on tile-local bits
-  uint32_t lout_m, lout_v;       // output pins on tile-local bits
-  int node;
-  uint64_t path;
-};
-
-__device__ __forceinline__ ItemGeo item_geo(const PassLaunch& P, int64_t item, int tiles_log2) {
-  const DevPass& d = P.pass;
-  ItemGeo g;
-  g.node = (int)(item >> tiles_log2);
-  const uint32_t t = (uint32_t)(item & ((1ll << tiles_log2) - 1));
-  g.path = P.nodes[g.node].path;
-  uint32_t base = 0;
-  for (int i = 0; i < d.n_free; i++) base |= ((t >> i) & 1u) << d.freepos[i];
-  uint32_t active = 0;
-  for (int j = 0; j < d.k; j++) active |= 1u << d.gpos[j];
-  uint32_t pm = 0, pv = 0, om = 0, ov = 0;
-  for (int i = 0; i < d.n_pin_in; i++) {
-    const uint32_t b = 1u << d.pin_in[i].pos;
-    pm |= b;
-    if (pin_val(d.pin_in[i], P.xshift, P.xbits, g.path)) pv |= b;
-  }
-  for (int i = 0; i < d.n_pin_out; i++) {
-    const uint32_t b = 1u << d.pin_out[i].pos;
-    om |= b;
-    if (pin_val(d.pin_out[i], P.xshift, P.xbits, g.path)) ov |= b;
-  }
-  g.base = base | (pv & ~active);
-  g.lin_m = g.lin_v = g.lout_m = g.lout_v = 0;
-  for (int j = 0; j < d.k; j++) {
-    const uint32_t gb = 1u << d.gpos[j];
-    if (pm & gb) {
-      g.lin_m |= 1u << j;
-      if (pv & gb) g.lin_v |= 1u << j;
-    }
-    if (om & gb) {
-      g.lout_m |= 1u << j;
-      if (ov & gb) g.lout_v |= 1u << j;
-    }
-  }
-  return g;
-}
-
-__device__ __forceinline__ void compute_bar(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
-__device__ __forceinline__ bool compute_bar_or(int nthreads, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(nthreads)
-      : "memory");
-  return r != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 
 template <int R, bool GEN>
 __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
-                                           float post_scale, int ncomp) {
+                                           int ncomp) {
+  const float post_scale = P.pass.post_scale;
   const DevPass& d = P.pass;
   const int k = d.k;
   for (int s = 0; s < d.n_stages; s++) {
@@ -413,164 +219,19 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
   }
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-// the barrier's pending count drops by one when this thread's earlier
-// cp.async copies have landed
-__device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
+// The generic stage program: reads the pass's stages, ops and phase groups
+// from the launch record and dispatches on them.
+template <int R, bool GEN>
+struct GenericProg {
+  static __device__ __forceinline__ void run(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
+                                             int ncomp) {
+    run_stages<R, GEN>(P, sm, g, w8, ncomp);
+  }
+};
 
-// Persistent fused pass, warp-specialised. Each CTA walks work items
-// (node, tile) with stride gridDim.x through NBUF shared-memory tile buffers.
-// Warp roles: compute warps run the register stages; a load warp streams the
-// next tiles in with 16-byte cp.async copies (one warp instruction moves 512
-// contiguous-run bytes; completion arrives on full[b]); a store warp streams
-// finished tiles out with 16-byte vector stores once the compute warps arrive
-// on empty[b], then frees the buffer (free[b]). Input-pinned (structurally
-// zero) runs are never read and output-pinned runs never written. Every wait
-// is bounded; a timeout sets the error flag and ends the kernel.
 template <int R, bool GEN>
 __global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
-  constexpr int NBUF = 3;
-  extern __shared__ __align__(128) unsigned char smem[];
-  const DevPass& d = P.pass;
-  const int k = d.k, L = d.L;
-  const int ntile = 1 << k, nruns = 1 << (k - L);
-  const int nact = 1 << (k - R);                 // compute threads doing stage work
-  const int ncw = (nact + 31) >> 5;               // compute warps
-  const int ncomp = ncw * 32;
-  float2* bufs = reinterpret_cast<float2*>(smem);
-  uint32_t* runoff = reinterpret_cast<uint32_t*>(bufs + NBUF * ntile);
-  uint64_t* full = reinterpret_cast<uint64_t*>(runoff + ((nruns + 1) & ~1));
-  uint64_t* empty = full + NBUF;
-  uint64_t* freeb = empty + NBUF;
-  __shared__ float2 w8[8];
-  __shared__ int abort_flag;
-  const int tiles_log2 = d.n_free;
-  const int64_t items = (int64_t)P.n_nodes << tiles_log2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nchunk = ntile >> 1;                  // 16-byte chunks per tile
-  const int lmask = (1 << L) - 1;
-
-  if (threadIdx.x < 8) {
-    const float r = 0.70710678118654752f;
-    const float c = (threadIdx.x & 1) ? r : 1.0f;
-    const int t = threadIdx.x;
-    float re = (t == 0) ? 1.f : (t == 2 || t == 6) ? 0.f : (t == 4) ? -1.f : (t == 1 || t == 7) ? c : -c;
-    float im = (t == 2) ? 1.f : (t == 6) ? -1.f : (t == 0 || t == 4) ? 0.f : (t == 1 || t == 3) ? c : -c;
-    w8[t] = make_float2(re, im);
-  }
-  for (int rI = threadIdx.x; rI < nruns; rI += blockDim.x) {
-    uint32_t hi = 0;
-    for (int j = L; j < k; j++) hi |= (uint32_t)((rI >> (j - L)) & 1) << d.gpos[j];
-    runoff[rI] = hi;
-  }
-  if (threadIdx.x == 0) {
-    abort_flag = 0;
-    for (int b = 0; b < NBUF; b++) {
-      mbar_init(smem_u32(&full[b]), 32);
-      mbar_init(smem_u32(&empty[b]), ncw);
-      mbar_init(smem_u32(&freeb[b]), 1);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-
-  if (warp == ncw) {
-    // --------------------------------------------------------------- loads
-    int i = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
-      const int b = i % NBUF;
-      if (i >= NBUF && !mbar_wait(smem_u32(&freeb[b]), (uint32_t)((i / NBUF - 1) & 1))) {
-        if (lane == 0) {
-          abort_flag = 1;
-          atomicExch(P.err, 1);
-        }
-        break;
-      }
-      if (*(volatile int*)&abort_flag) break;
-      if (!d.gen_input) {
-        const ItemGeo g = item_geo(P, it, tiles_log2);
-        const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
-        const uint32_t dst = smem_u32(bufs + b * ntile);
-        const uint32_t rm = g.lin_m >> L, rv = g.lin_v >> L;
-        for (int c = lane; c < nchunk; c += 32) {
-          const int e = c << 1, r = e >> L;
-          if (((uint32_t)r & rm) != rv) continue;
-          cp_async16(dst + swz((uint32_t)e) * 8u, in + (g.base | runoff[r] | (uint32_t)(e & lmask)));
-        }
-      }
-      cp_async_arrive(smem_u32(&full[b]));
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    return;
-  }
-  if (warp == ncw + 1) {
-    // -------------------------------------------------------------- stores
-    int i = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
-      const int b = i % NBUF;
-      if (!mbar_wait(smem_u32(&empty[b]), (uint32_t)((i / NBUF) & 1)) || *(volatile int*)&abort_flag) {
-        if (lane == 0) {
-          abort_flag = 1;
-          atomicExch(P.err, 1);
-        }
-        break;
-      }
-      const ItemGeo g = item_geo(P, it, tiles_log2);
-      float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
-      const float4* src = reinterpret_cast<const float4*>(bufs + b * ntile);
-      const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
-      for (int c = lane; c < nchunk; c += 32) {
-        const int e = c << 1, r = e >> L;
-        if (((uint32_t)r & rm) != rv) continue;
-        const float4 v = src[swz((uint32_t)e) >> 1];
-        *reinterpret_cast<float4*>(out + (g.base | runoff[r] | (uint32_t)(e & lmask))) = v;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&freeb[b]));
-    }
-    return;
-  }
-
-  // -------------------------------------------------------------- compute
-  int i = 0;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
-    const int b = i % NBUF;
-    float2* sm = bufs + b * ntile;
-    const ItemGeo g = item_geo(P, it, tiles_log2);
-    const bool timed_out = !mbar_wait(smem_u32(&full[b]), (uint32_t)((i / NBUF) & 1));
-    if (compute_bar_or(ncomp, timed_out || *(volatile int*)&abort_flag)) {
-      if (threadIdx.x == 0) {
-        abort_flag = 1;
-        atomicExch(P.err, 1);
-      }
-      break;
-    }
-    if (d.gen_input) {
-      for (int e = threadIdx.x; e < ntile; e += ncomp)
-        sm[swz(e)] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-      compute_bar(ncomp);
-    } else if (g.lin_m) {
-      for (int e = threadIdx.x; e < ntile; e += ncomp)
-        if (((uint32_t)e & g.lin_m) != g.lin_v) sm[swz(e)] = make_float2(0.f, 0.f);
-      compute_bar(ncomp);
-    }
-    if (threadIdx.x < nact) run_stages<R, GEN>(P, sm, g, w8, d.post_scale, ncomp);
-    else
-      for (int s = 0; s < d.n_stages; s++) compute_bar(ncomp);
-    if (d.n_stages == 0 && d.post_scale != 1.0f) {
-      for (int e = threadIdx.x; e < ntile; e += ncomp) {
-        float2 v = sm[e];
-        sm[e] = make_float2(v.x * d.post_scale, v.y * d.post_scale);
-      }
-      compute_bar(ncomp);
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(smem_u32(&empty[b]));
-  }
+  pass_body<R, GenericProg<R, GEN>>(P);
 }
 
 // ------------------------------------------------------------------ gather

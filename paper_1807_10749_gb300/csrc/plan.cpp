@@ -195,7 +195,7 @@ HOp local_op(const Gate& g, int p0, int p1, cd& global) {
   if (g.kind == SF_H || g.kind == SF_X_HALF || g.kind == SF_Y_HALF) {
     o.kind = H_G1;
     o.fast = g.kind == SF_H ? DOP_H : (g.kind == SF_X_HALF ? DOP_XH : DOP_YH);
-    o.scale_e = g.kind == SF_H ? 1 : 2;
+    o.scale_e = 1;  // H = M_H / sqrt2; X^1/2, Y^1/2 = e^{i pi/4} M / sqrt2
     return o;
   }
   bool diag = near(m[1], 0, 0) && near(m[2], 0, 0);
@@ -652,9 +652,12 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
       for (size_t i = 0; i < pout.size(); i++) dp.pin_out[i] = to_dev(pout[i]);
       dp.gen_input = (first && gen_input) ? 1 : 0;
       // scale bookkeeping (exact powers of two applied in the pass)
-      int e = 0;
+      int e = 0, nxy = 0;
       for (const HOp* o : taken)
-        if (o->kind == H_G1 && o->fast) e += o->scale_e;
+        if (o->kind == H_G1 && o->fast) {
+          e += o->scale_e;
+          if (o->fast != DOP_H) nxy++;
+        }
       int t = res + e;
       int shift = t / 2;
       dp.post_scale = std::ldexp(1.0f, -shift);
@@ -719,7 +722,7 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
       }
       if (ok) {
         res = t - 2 * shift;
-        sigma *= std::pow(2.0, -0.5 * e) / std::ldexp(1.0, -shift);
+        sigma *= std::pow(2.0, -0.5 * e) / std::ldexp(1.0, -shift) * std::polar(1.0, M_PI / 4 * (nxy % 8));
         break;
       }
       if (cap <= 1) fail(SF_EUNSUPPORTED, "a single gate exceeds the pass program limits");

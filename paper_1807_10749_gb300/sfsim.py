@@ -50,7 +50,7 @@ class sf_plan_opts(ctypes.Structure):
                 ("fuse_bits", ctypes.c_int32), ("exec_mode", ctypes.c_int32),
                 ("defer_last_level", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("batch_paths", ctypes.c_int32), ("run_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("jit", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class sf_path_sel(ctypes.Structure):
@@ -361,6 +361,7 @@ class Plan:
             self.handle = sf_plan_create(self.circuit, sf_plan_opts_default(**opts))
         except Exception:
             sf_circuit_destroy(self.circuit)
+            self.circuit = None
             raise
         self.info = sf_plan_info(self.handle)
 

@@ -29,6 +29,13 @@ def built():
     sim.build()
 
 
+@pytest.fixture(params=[0, 1], ids=["generic", "specialised"])
+def jit(request):
+    """Both pass-kernel forms: the generic kernel and the per-pass specialised
+    kernels compiled at plan time."""
+    return request.param
+
+
 def check_close(gpu, ref, n, label="", nonzero=True):
     err = np.abs(gpu - ref)
     rms = np.sqrt(np.mean(np.abs(ref) ** 2))
@@ -46,12 +53,12 @@ def workload(name, **kw):
 
 
 # ----------------------------------------------------------------- 4x4 (C1)
-def test_4x4_all_paths_equal_state_vector():
+def test_4x4_all_paths_equal_state_vector(jit):
     w, text = workload("4x4_d10")
     c = ocirc.parse(text)
     xs = np.arange(1 << 16, dtype=np.uint64)
     ref = sim.sv_amplitudes(c, xs)
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     amp, fa = p.amplitudes(xs, sfsim.selection("fraction", fidelity=1.0))
     assert fa == 1.0
     check_close(amp, ref, 16, "4x4 f=1 all bitstrings")
@@ -61,13 +68,13 @@ def test_4x4_all_paths_equal_state_vector():
     p.close()
 
 
-def test_4x4_each_path_alone_matches_oracle():
+def test_4x4_each_path_alone_matches_oracle(jit):
     """Per-path parity: path numbering and enumeration agree exactly."""
     w, text = workload("4x4_d10")
     c = ocirc.parse(text)
     setup = sim.SFSetup(c, w["side_b_mask"])
     bits = inputs.random_bitstrings(16, 1024, w["bitstring_seed"])
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     for j in range(16):
         ref = sim.sf_amplitudes(setup, np.array([j], dtype=np.uint64), bits)
         amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=[j]))
@@ -77,13 +84,13 @@ def test_4x4_each_path_alone_matches_oracle():
 
 @pytest.mark.parametrize("kind,dec", [("haar", sfsim.SF_DEC_SCHMIDT), ("haar", sfsim.SF_DEC_BLOCK4),
                                       ("iswap", sfsim.SF_DEC_BLOCK4)])
-def test_4x4_four_way_branching(kind, dec):
+def test_4x4_four_way_branching(kind, dec, jit):
     """Section 7: non-CZ cross gates branch four ways (Schmidt / Eq. 4way)."""
     w, text = workload("4x4_d10", haar=(kind == "haar"), iswap=(kind == "iswap"))
     c = ocirc.parse(text)
     xs = np.arange(1 << 16, dtype=np.uint64)
     ref = sim.sv_amplitudes(c, xs)
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"], decomposition=dec)
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], decomposition=dec)
     amp, _ = p.amplitudes(xs, sfsim.selection("fraction", fidelity=1.0))
     check_close(amp, ref, 16, f"4x4 {kind} dec={dec}")
     # per-path parity for a few paths (tie-free decompositions)
@@ -97,11 +104,11 @@ def test_4x4_four_way_branching(kind, dec):
     p.close()
 
 
-def test_4x4_plain_equals_batched():
+def test_4x4_plain_equals_batched(jit):
     w, text = workload("4x4_d10")
     bits = inputs.random_bitstrings(16, 1024, w["bitstring_seed"])
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
-    q = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN)
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
+    q = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN)
     sel = sfsim.selection("fraction", fidelity=1.0)
     a, _ = p.amplitudes(bits, sel)
     b, _ = q.amplitudes(bits, sel)
@@ -110,9 +117,9 @@ def test_4x4_plain_equals_batched():
     q.close()
 
 
-def test_edge_cases():
+def test_edge_cases(jit):
     w, text = workload("4x4_d10")
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     c = ocirc.parse(text)
     # empty bitstring list, empty selection
     a, _ = p.amplitudes(np.zeros(0, dtype=np.uint64), sfsim.selection("range", count=16))
@@ -151,12 +158,12 @@ def test_device_form_matches_host_form():
 
 
 # ---------------------------------------------------------------- 5x6 (C2)
-def test_5x6_path_subsets_match_oracle():
+def test_5x6_path_subsets_match_oracle(jit):
     w, text = workload("5x6_d24")
     c = ocirc.parse(text)
     setup = sim.SFSetup(c, w["side_b_mask"])
     bits = inputs.random_bitstrings(30, 20000, w["bitstring_seed"])
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     for sel, ids in [(sfsim.selection("range", first=5000, count=700), opaths.select_range(5000, 700)),
                      (sfsim.selection("fraction", fidelity=1 / 32, seed=7),
                       opaths.select_fraction(setup.x_bits, 1 / 32, 7)[0])]:
@@ -166,11 +173,11 @@ def test_5x6_path_subsets_match_oracle():
     p.close()
 
 
-def test_5x6_full_sum_porter_thomas():
+def test_5x6_full_sum_porter_thomas(jit):
     """All 2^15 paths, 100k bitstrings: E[N p] ~ 1, E[(N p)^2] ~ 2 (Section 4)."""
     w, text = workload("5x6_d24")
     bits = inputs.random_bitstrings(30, w["n_bitstrings"], w["bitstring_seed"])
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     amp, _ = p.amplitudes(bits, sfsim.selection("fraction", fidelity=1.0))
     t = (2.0 ** 30) * np.abs(amp) ** 2
     print("5x6 PT moments", t.mean(), (t ** 2).mean())
@@ -181,7 +188,7 @@ def test_5x6_full_sum_porter_thomas():
 
 # ---------------------------------------------------------------- 6x7 (C3)
 @pytest.mark.parametrize("kind", ["cz", "haar"])
-def test_6x7_path_list_matches_oracle(kind):
+def test_6x7_path_list_matches_oracle(kind, jit):
     w, text = workload("6x7_d26", haar=(kind == "haar"))
     c = ocirc.parse(text)
     setup = sim.SFSetup(c, w["side_b_mask"])
@@ -194,14 +201,14 @@ def test_6x7_path_list_matches_oracle(kind):
     if kind == "haar":
         ids = np.unique(np.concatenate([ids[:6], full[:40]]))
     ref = sim.sf_amplitudes(setup, ids, bits)
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
     check_close(amp, ref, 42, f"6x7 {kind} {len(ids)} paths")
     p.close()
 
 
 # ---------------------------------------------------------------- 7x8 (C4)
-def test_7x8_path_list_matches_oracle():
+def test_7x8_path_list_matches_oracle(jit):
     """Full size (28+28 qubits, 2 GiB halves): a seeded path list x 1024
     bitstrings against the oracle (v2 circuit: every path is non-zero)."""
     w, text = workload("7x8_d40")
@@ -210,20 +217,20 @@ def test_7x8_path_list_matches_oracle():
     bits = inputs.random_bitstrings(56, 1024, w["bitstring_seed"])
     ids = inputs.random_path_list(setup.x_bits, 2, 8)
     ref = sim.sf_amplitudes(setup, ids, bits)
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
     check_close(amp, ref, 56, "7x8 2 paths")
     p.close()
 
 
-def test_7x8_prefix_batched_equals_plain():
+def test_7x8_prefix_batched_equals_plain(jit):
     """One 128-path prefix of the f = 0.5% selection: the batched executor
     (path tree + last level folded into the gather) equals the plain
     one-path-at-a-time executor."""
     w, text = workload("7x8_d40")
     bits = inputs.random_bitstrings(56, 100000, w["bitstring_seed"])
-    p = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
-    q = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN)
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
+    q = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], exec_mode=sfsim.SF_EXEC_PLAIN)
     ids = sfsim.sf_selection_ids(p.handle, sfsim.selection("fraction", fidelity=0.005, seed=7), cap=128)
     sel = sfsim.selection("range", first=int(ids[0]), count=128)
     a, _ = p.amplitudes(bits, sel)

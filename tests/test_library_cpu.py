@@ -121,3 +121,25 @@ def test_feistel_matches_oracle_at_28_bits():
     want = np.array([(q << 7) | s for q in pre for s in range(128)], dtype=np.uint64)
     assert np.array_equal(ids, want)
     p.close()
+
+
+@pytest.mark.parametrize("name", ["4x4_d10", "6x7_d26", "7x8_d40"])
+def test_specialised_pass_kernels_compile(name):
+    """Every pass of the plan compiles into its own kernel (NVRTC runs
+    without a GPU); a second plan of the same circuit reuses the binaries."""
+    import time
+    w = inputs.WORKLOADS[name]
+    text = inputs.workload_circuit(name).text()
+    try:
+        p = sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=1)
+    except sfsim.SFError as e:
+        if e.code == sfsim.SF_EUNSUPPORTED:
+            pytest.skip(str(e))
+        raise
+    p.close()
+    t = time.perf_counter()
+    q = sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=1)
+    assert time.perf_counter() - t < 2.0   # cached
+    q.close()
+    with pytest.raises(sfsim.SFError):
+        sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=2)
