@@ -335,8 +335,16 @@ void compile_entry(Entry* e) {
     e->compiled = true;
     return;
   }
-  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG"};
-  const nvrtcResult rc = n.compile(prog, 4, opts);
+  const bool verbose = std::getenv("SF_JIT_VERBOSE") != nullptr;
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DNDEBUG", "--ptxas-options=-v"};
+  const nvrtcResult rc = n.compile(prog, verbose ? 5 : 4, opts);
+  if (verbose && rc == 0) {
+    size_t ls = 0;
+    n.log_size(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) n.log(prog, &log[0]);
+    std::fprintf(stderr, "%s\n", log.c_str());
+  }
   if (rc != 0) {
     size_t ls = 0;
     n.log_size(prog, &ls);

@@ -242,6 +242,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
   uint64_t* freeb = empty + NBUF;
   __shared__ float2 w8[8];
   __shared__ int abort_flag;
+  __shared__ ItemGeo geo[NBUF];  // geometry of the item in buffer b
   const int tiles_log2 = d.n_free;
   const int64_t items = (int64_t)P.n_nodes << tiles_log2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -264,7 +265,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int b = 0; b < NBUF; b++) {
-      mbar_init(smem_u32(&full[b]), 32);
+      mbar_init(smem_u32(&full[b]), 33);  // 32 copy arrivals + the geometry
       mbar_init(smem_u32(&empty[b]), ncw);
       mbar_init(smem_u32(&freeb[b]), 1);
     }
@@ -274,6 +275,9 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
 
   if (warp == ncw) {
     // --------------------------------------------------------------- loads
+    // The load warp also computes each item's geometry once and publishes it
+    // in geo[b]; lane 0's arrive (release) on full[b] orders it before the
+    // compute and store warps' waits (acquire) on that barrier.
     int i = 0;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
       const int b = i % NBUF;
@@ -285,18 +289,32 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         break;
       }
       if (*(volatile int*)&abort_flag) break;
+      const ItemGeo g = item_geo(P, it, tiles_log2);
+      if (lane == 0) geo[b] = g;
       if (!d.gen_input) {
-        const ItemGeo g = item_geo(P, it, tiles_log2);
         const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
         const uint32_t dst = smem_u32(bufs + b * ntile);
         const uint32_t rm = g.lin_m >> L, rv = g.lin_v >> L;
-        for (int c = lane; c < nchunk; c += 32) {
-          const int e = c << 1, r = e >> L;
-          if (((uint32_t)r & rm) != rv) continue;
-          cp_async16(dst + swz((uint32_t)e) * 8u, in + (g.base | runoff[r] | (uint32_t)(e & lmask)));
+        for (int c0 = lane; c0 < nchunk; c0 += 128) {
+          uint32_t so[4];
+          const float2* src[4];
+          bool ok[4];
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int c = c0 + 32 * u;
+            const int e = c << 1, r = e >> L;
+            ok[u] = c < nchunk && (((uint32_t)r & rm) == rv);
+            so[u] = swz((uint32_t)e) * 8u;
+            src[u] = in + (g.base | runoff[ok[u] ? r : 0] | (uint32_t)(e & lmask));
+          }
+#pragma unroll
+          for (int u = 0; u < 4; u++)
+            if (ok[u]) cp_async16(dst + so[u], src[u]);
         }
       }
       cp_async_arrive(smem_u32(&full[b]));
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&full[b]));
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     return;
@@ -313,15 +331,25 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         }
         break;
       }
-      const ItemGeo g = item_geo(P, it, tiles_log2);
+      const ItemGeo g = geo[b];
       float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
-      const float4* src = reinterpret_cast<const float4*>(bufs + b * ntile);
+      const float4* srcb = reinterpret_cast<const float4*>(bufs + b * ntile);
       const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
-      for (int c = lane; c < nchunk; c += 32) {
-        const int e = c << 1, r = e >> L;
-        if (((uint32_t)r & rm) != rv) continue;
-        const float4 v = src[swz((uint32_t)e) >> 1];
-        *reinterpret_cast<float4*>(out + (g.base | runoff[r] | (uint32_t)(e & lmask))) = v;
+      for (int c0 = lane; c0 < nchunk; c0 += 128) {
+        float4 v[4];
+        float2* dst[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int c = c0 + 32 * u;
+          const int e = c << 1, r = e >> L;
+          ok[u] = c < nchunk && (((uint32_t)r & rm) == rv);
+          v[u] = srcb[swz((uint32_t)(ok[u] ? e : 0)) >> 1];
+          dst[u] = out + (g.base | runoff[ok[u] ? r : 0] | (uint32_t)(e & lmask));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (ok[u]) *reinterpret_cast<float4*>(dst[u]) = v[u];
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&freeb[b]));
@@ -334,7 +362,6 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
     const int b = i % NBUF;
     float2* sm = bufs + b * ntile;
-    const ItemGeo g = item_geo(P, it, tiles_log2);
     const bool timed_out = !mbar_wait(smem_u32(&full[b]), (uint32_t)((i / NBUF) & 1));
     if (compute_bar_or(ncomp, timed_out || *(volatile int*)&abort_flag)) {
       if (threadIdx.x == 0) {
@@ -343,6 +370,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
       }
       break;
     }
+    const ItemGeo g = geo[b];
     if (d.gen_input) {
       for (int e = threadIdx.x; e < ntile; e += ncomp)
         sm[swz(e)] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);

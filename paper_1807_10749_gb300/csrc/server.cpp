@@ -37,6 +37,7 @@ struct Request {
   sf_path_sel sel;
   size_t ws_bytes = 0;
   int64_t footprint = 0;
+  double terms[3] = {0, 0, 0};  // runtime-model features (Eq. t_tot)
   std::vector<double> out;
   int state = Q_QUEUED;
   int err_code = 0;
@@ -59,6 +60,10 @@ struct sf_server {
   bool stop = false;
   uint64_t next_ticket = 1;
   std::vector<std::thread> workers;
+  // runtime model: when set, admission prefers the shortest predicted request
+  bool model = false;
+  double coeffs[3] = {0, 0, 0};
+  double max_wait_s = 1.0;
 };
 
 namespace {
@@ -69,10 +74,39 @@ void cuda_ok(cudaError_t e, const char* what) {
 }
 
 // Pick the next request to admit (caller holds the lock): the oldest one that
-// fits, unless the oldest has waited > 1 s and does not fit.
+// fits, unless the oldest has waited > 1 s and does not fit. With a runtime
+// model set, requests that have waited less than max_wait_s go in order of
+// predicted time (shortest first) after any that have waited longer.
 std::shared_ptr<Request> pick(sf_server& s) {
   if (s.queue.empty()) return nullptr;
   auto now = Clock::now();
+  if (s.model) {
+    const auto aged = std::chrono::duration<double>(s.max_wait_s);
+    int best = -1;
+    double best_t = 0;
+    for (size_t i = 0; i < s.queue.size(); i++) {
+      auto& r = s.queue[i];
+      const bool old = now - r->t_submit > aged;
+      const bool fits = s.in_use + r->footprint <= s.budget || s.running == 0;
+      if (old) {
+        if (best >= 0 && now - s.queue[best]->t_submit > aged) continue;  // an older aged one wins
+        if (!fits) return nullptr;  // the oldest aged request blocks until memory frees
+        best = (int)i;
+        best_t = -1;
+        continue;
+      }
+      if (!fits || (best >= 0 && best_t < 0)) continue;
+      const double t = sf_cost_predict(r->terms, s.coeffs);
+      if (best < 0 || t < best_t) {
+        best = (int)i;
+        best_t = t;
+      }
+    }
+    if (best < 0) return nullptr;
+    auto out = s.queue[best];
+    s.queue.erase(s.queue.begin() + best);
+    return out;
+  }
   for (size_t i = 0; i < s.queue.size(); i++) {
     auto& r = s.queue[i];
     if (s.in_use + r->footprint <= s.budget || s.running == 0) {
@@ -216,6 +250,7 @@ int sf_server_submit(sf_server* s, sf_plan* p, const uint64_t* bits, int64_t n, 
   }
   r->ws_bytes = sf::exec_workspace_bytes(*r->plan, n, r->sel);
   r->footprint = (int64_t)r->ws_bytes + 24 * n;
+  sf::cost_terms(*r->plan, r->sel, n, r->terms);
   if (r->footprint > s->budget)
     sf::fail(SF_ENOMEM, "request footprint " + std::to_string(r->footprint) + " exceeds the server budget");
   {
@@ -270,6 +305,21 @@ int sf_server_cancel(sf_server* s, uint64_t ticket) {
     }
   }
   s->cv_done.notify_all();
+  return SF_OK;
+  SF_SGUARD_END
+}
+
+int sf_server_set_cost_model(sf_server* s, const double* coeffs, double max_wait_s) {
+  SF_SGUARD_BEGIN
+  if (!s || !(max_wait_s >= 0)) sf::fail(SF_EINVAL, "bad argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->model = coeffs != nullptr;
+  if (coeffs)
+    for (int j = 0; j < 3; j++) {
+      if (!(coeffs[j] >= 0)) sf::fail(SF_EINVAL, "model coefficients must be >= 0");
+      s->coeffs[j] = coeffs[j];
+    }
+  s->max_wait_s = max_wait_s;
   return SF_OK;
   SF_SGUARD_END
 }

@@ -29,7 +29,7 @@ EXPORTED = [
     "sf_server_cancel", "sf_server_times", "sf_server_destroy", "sf_plan_profile",
     "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_plan_segment_stats",
     "sf_plan_describe", "sf_frugal_accept_device", "sf_plan_autotune", "sf_overlap_device",
-    "sf_last_error",
+    "sf_plan_cost_terms", "sf_cost_fit", "sf_cost_predict", "sf_server_set_cost_model", "sf_last_error",
 ]
 
 
@@ -101,6 +101,10 @@ def lib():
                                               P, P, P]),
             "sf_plan_autotune": (i32, [P, P, P, i64, P, i64, P, P]),
             "sf_overlap_device": (i32, [P, P, i64, P, P]),
+            "sf_plan_cost_terms": (i32, [P, P, i64, P]),
+            "sf_cost_fit": (i32, [P, P, i64, P]),
+            "sf_cost_predict": (ctypes.c_double, [P, P]),
+            "sf_server_set_cost_model": (i32, [P, P, ctypes.c_double]),
             "sf_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -345,6 +349,36 @@ def fidelity_estimate(sums):
     """f_e = |<a|b>|^2 / (<a|a><b|b>) from the four sums of sf_overlap_device."""
     re, im, na, nb = [float(v) for v in sums]
     return (re * re + im * im) / (na * nb)
+
+
+def sf_plan_cost_terms(plan, sel, n_a):
+    """The three features (t0, t1, t2) of the runtime model for a request."""
+    t = (ctypes.c_double * 3)()
+    _check(lib().sf_plan_cost_terms(plan, ctypes.byref(sel), n_a, t))
+    return np.array(t[:], dtype=np.float64)
+
+
+def sf_cost_fit(terms, seconds):
+    """Fit (C1, C1*C2, C3) >= 0 from an (n, 3) feature array and n times."""
+    t = np.ascontiguousarray(terms, dtype=np.float64)
+    s = np.ascontiguousarray(seconds, dtype=np.float64)
+    c = (ctypes.c_double * 3)()
+    _check(lib().sf_cost_fit(_ptr(t), _ptr(s), len(s), c))
+    return np.array(c[:], dtype=np.float64)
+
+
+def sf_cost_predict(terms, coeffs):
+    t = np.ascontiguousarray(terms, dtype=np.float64)
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    return float(lib().sf_cost_predict(_ptr(t), _ptr(c)))
+
+
+def sf_server_set_cost_model(server, coeffs, max_wait_s=1.0):
+    if coeffs is None:
+        _check(lib().sf_server_set_cost_model(server, None, max_wait_s))
+    else:
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        _check(lib().sf_server_set_cost_model(server, _ptr(c), max_wait_s))
 
 
 def sf_last_error() -> str:

@@ -143,3 +143,49 @@ def test_specialised_pass_kernels_compile(name):
     q.close()
     with pytest.raises(sfsim.SFError):
         sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=2)
+
+
+def test_cost_terms_follow_eq_t_tot():
+    """Features of the runtime model (Section 8) for the 5x6, 1+24+1 circuit,
+    recomputed here from the circuit text: q1 = q2 = 15, x = 15 cross gates,
+    x_p = 8 prefix bits (x_b = 7), d = 26 cycles, d_p = the cycle of the
+    8th cross gate in time order."""
+    w = inputs.WORKLOADS["5x6_d24"]
+    text = inputs.workload_circuit("5x6_d24").text()
+    c = ocirc.parse(text)
+    mask = w["side_b_mask"]
+    inB = lambda q: (mask >> q) & 1
+    cross = sorted([g for g in c.gates if len(g.qubits) == 2 and inB(g.qubits[0]) != inB(g.qubits[1])],
+                   key=lambda g: (g.cycle, min(g.qubits), max(g.qubits)))
+    assert len(cross) == 15
+    d = max(g.cycle for g in c.gates) + 1
+    dp = cross[15 - 1 - 7].cycle       # path bit 7 <-> cross gate 7 (earliest in the MSB)
+    work = 2 * 15 * 2.0 ** 15
+    p = sfsim.Plan(text, side_b_mask=mask)
+    n_a = 1000
+    t = sfsim.sf_plan_cost_terms(p.handle, sfsim.selection("fraction", fidelity=0.25, seed=7), n_a)
+    K = 64   # floor(0.25 * 2^8) prefixes of 2^7 paths
+    assert np.allclose(t, [K * work * dp, K * work * 128 * (d - dp), K * 128 * n_a], rtol=1e-12)
+    # a range inside one prefix: one prefix, 10 paths
+    t = sfsim.sf_plan_cost_terms(p.handle, sfsim.selection("range", first=300, count=10), n_a)
+    assert np.allclose(t, [work * dp, work * 128 * (d - dp), 10 * n_a], rtol=1e-12)
+    # a range over a prefix boundary: two prefixes
+    t = sfsim.sf_plan_cost_terms(p.handle, sfsim.selection("range", first=250, count=10), n_a)
+    assert np.isclose(t[0], 2 * work * dp)
+    p.close()
+
+
+def test_cost_fit_recovers_coefficients():
+    rng = np.random.default_rng(4)
+    T = rng.uniform(0.0, 1.0, size=(12, 3)) * np.array([1e9, 1e11, 1e8])
+    a = np.array([2e-12, 3e-14, 5e-10])
+    secs = T @ a
+    got = sfsim.sf_cost_fit(T, secs)
+    assert np.allclose(got, a, rtol=1e-8)
+    assert abs(sfsim.sf_cost_predict(T[0], got) - secs[0]) <= 1e-9 * secs[0]
+    # a coefficient that would come out negative is clipped to zero
+    secs2 = T[:, 0] * 2e-12 + T[:, 2] * 5e-10
+    got2 = sfsim.sf_cost_fit(T, secs2)
+    assert got2[1] == 0.0 and np.allclose(got2[[0, 2]], [2e-12, 5e-10], rtol=1e-8)
+    with pytest.raises(sfsim.SFError):
+        sfsim.sf_cost_fit(T, -secs)

@@ -42,7 +42,9 @@ def test_overlap_sums_match_oracle(n):
 @pytest.fixture(scope="module")
 def c2():
     w = inputs.WORKLOADS["5x6_d24"]
-    plan = sfsim.Plan(inputs.workload_circuit("5x6_d24").text(), side_b_mask=w["side_b_mask"])
+    # path-level selection (x_s = x = 15): a random fraction f of the paths
+    plan = sfsim.Plan(inputs.workload_circuit("5x6_d24").text(), side_b_mask=w["side_b_mask"],
+                      select_prefix_bits=15)
     bits = inputs.random_bitstrings(30, w["n_bitstrings"], 77)   # the Verifier's seeded indices
     exact, _ = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=1.0))
     yield plan, bits, exact
@@ -51,15 +53,19 @@ def c2():
 
 @pytest.mark.parametrize("f", [1 / 4, 1 / 16, 1 / 64])
 def test_fidelity_estimate_tracks_f_actual(c2, f):
-    """The exact Claimant against a Verifier at fidelity f: f_e within 10% of
-    f_actual, and within 0.02 of the Verifier's own estimate 2^n E|v|^2."""
+    """The exact Claimant against a Verifier that sums a random fraction f of
+    the paths: f_e within max(10%, 3/sqrt(K)) of f_actual (K selected paths;
+    a statistical check, Section 3 and Fig. 5), and within 0.02 of the
+    Verifier's own estimate 2^n E|v|^2."""
     plan, bits, exact = c2
     ver, f_actual = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=f, seed=5))
+    K = f_actual * 2 ** 15
     sums = _overlap(exact, ver)
     np.testing.assert_allclose(sums, validation.overlap_sums(exact, ver), rtol=1e-10)
     fe = sfsim.fidelity_estimate(sums)
     f1 = 2.0 ** 30 * np.mean(np.abs(ver) ** 2)
-    assert abs(fe - f_actual) <= 0.1 * f_actual, (fe, f_actual)
+    print(f"f = {f}: f_e = {fe:.4f}, f_actual = {f_actual:.4f}, K = {K:.0f}")
+    assert abs(fe - f_actual) <= max(0.1, 3 / np.sqrt(K)) * f_actual, (fe, f_actual)
     assert abs(fe - f1) <= 0.02 + 0.1 * f1, (fe, f1)
 
 
