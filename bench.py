@@ -423,7 +423,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
-                                              "tile_bits": args.tile_bits or 13, "fuse_bits": args.fuse_bits or 5,
+                                              "tile_bits": args.tile_bits or 12, "fuse_bits": args.fuse_bits or 5,
                                               "run_bits": args.run_bits or 3,
                                               "pass_kernels": "specialised" if args.jit else "generic",
                                               "plan_seconds": t_plan,

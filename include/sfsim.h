@@ -95,7 +95,7 @@ typedef struct {
                                 block, then the number of cross gates) */
   int32_t decomposition;     /* SF_DEC_* for non-CZ cross gates */
   int32_t select_prefix_bits;/* x_s of FRACTION selection; -1 = max(0, x-7) */
-  int32_t tile_bits;         /* log2 amplitudes per tile, 0 = tuned default */
+  int32_t tile_bits;         /* log2 amplitudes per tile (<= 13), 0 = 12 */
   int32_t fuse_bits;         /* log2 amplitudes per thread register block
                                 (fusion width), 0 = tuned default */
   int32_t exec_mode;         /* SF_EXEC_* */
@@ -170,19 +170,19 @@ SF_API int sf_plan_autotune(const sf_circuit* c, const sf_plan_opts* base, const
                             int64_t sample_paths, const uint64_t* d_bits, int64_t n, sf_plan_opts* best,
                             double* best_seconds);
 
-/* Runtime model of Section 8 (Eq. t_tot):
- *   T = C1 f 2^{x_p} (q1 2^{q1} + q2 2^{q2}) (d_p + C2 2^{x_b} d_b) + C3 P n_a
+/* Runtime model of Section 8 (Eq. t_tot), with a fixed cost per request:
+ *   T = C0 + C1 f 2^{x_p} (q1 2^{q1} + q2 2^{q2}) (d_p + C2 2^{x_b} d_b) + C3 P n_a
  * with q1, q2 the half sizes, x_p the selection prefix bits (select_prefix_bits),
  * x_b the path bits below them, f 2^{x_p} the selected prefixes, d_p the
  * cycles before the cycle of the last prefix cross gate, d_b the remaining
- * cycles, P the selected paths and n_a the bitstrings. The model is linear:
- *   T = a0 t0 + a1 t1 + a2 t2,  a = (C1, C1 C2, C3),
- * t0 = f 2^{x_p} (q1 2^{q1} + q2 2^{q2}) d_p, t1 = f 2^{x_p} (...) 2^{x_b} d_b,
- * t2 = P n_a.
- * sf_plan_cost_terms writes t0..t2 for a request (host only, no GPU work).
- * sf_cost_fit fits a (a >= 0, least squares on relative error) from n
- * requests' terms (3n doubles, row-major) and measured seconds; SF_EINVAL if
- * the set cannot determine any coefficient. sf_cost_predict returns a . t. */
+ * cycles, P the selected paths and n_a the bitstrings. C0 (launches, uploads,
+ * the final copy) is not in the paper's equation. The model is linear:
+ *   T = a . t,  a = (C0, C1, C1 C2, C3),
+ * t = (1, f 2^{x_p} (q1 2^{q1} + q2 2^{q2}) d_p, f 2^{x_p} (...) 2^{x_b} d_b, P n_a).
+ * sf_plan_cost_terms writes t (4 doubles) for a request (host only, no GPU
+ * work). sf_cost_fit fits a (a >= 0, least squares on relative error) from n
+ * requests' terms (4n doubles, row-major) and measured seconds; SF_EINVAL if
+ * the set determines no coefficient. sf_cost_predict returns a . t. */
 SF_API int sf_plan_cost_terms(const sf_plan* p, const sf_path_sel* sel, int64_t n_a, double* terms);
 SF_API int sf_cost_fit(const double* terms, const double* seconds, int64_t n, double* coeffs);
 SF_API double sf_cost_predict(const double* terms, const double* coeffs);
@@ -276,8 +276,8 @@ SF_API int sf_server_cancel(sf_server* s, uint64_t ticket);
 /* Seconds from submit to admission and to completion of a finished ticket
  * (before its wait), for latency reports. */
 SF_API int sf_server_times(sf_server* s, uint64_t ticket, double* queued_s, double* total_s);
-/* Admission by the runtime model (Section 8, Eq. t_tot): with coeffs (C1,
- * C1 C2, C3 as sf_cost_fit returns them) set, among the requests that fit the
+/* Admission by the runtime model (Section 8, Eq. t_tot): with coeffs (C0,
+ * C1, C1 C2, C3 as sf_cost_fit returns them) set, among the requests that fit the
  * budget the one with the shortest predicted time is admitted first; a
  * request queued longer than max_wait_s seconds goes before all others (in
  * arrival order) and, if it does not fit, blocks admission until memory

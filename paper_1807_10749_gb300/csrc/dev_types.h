@@ -93,8 +93,8 @@ struct DevPin {
 struct DevStage {
   int32_t r;
   int8_t rbit[MAX_R];  // tile-local bit index of register bit j
-  int8_t tpos[8];      // tile-local bit of thread-index bit i (k - r of them)
-  int8_t tg[8];        // global position of thread-index bit i
+  int8_t tpos[9];      // tile-local bit of thread-index bit i (k - r <= 9 of them)
+  int8_t tg[9];        // global position of thread-index bit i
   int32_t op_begin, op_end;
 };
 

@@ -284,7 +284,8 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     o << "compute_bar(ncomp);\n}\n";
   }
   o << "}\n};\n}  // namespace sf\n";
-  o << "extern \"C\" __global__ void __launch_bounds__(320, 1) " << name
+  const int threads = (((1 << (k - R)) + 31) / 32) * 32 + 64;  // stage warps + the two copy warps
+  o << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", 1) " << name
     << "(const __grid_constant__ sf::PassLaunch P) {\n  sf::pass_body<" << R << ", sf::" << name
     << "_prog>(P);\n}\n";
   return o.str();

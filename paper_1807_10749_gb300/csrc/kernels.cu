@@ -229,8 +229,9 @@ struct GenericProg {
   }
 };
 
+// Up to 2^(13-R) stage threads + the two copy warps: 320 at R = 5, 576 below.
 template <int R, bool GEN>
-__global__ void __launch_bounds__(320, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
+__global__ void __launch_bounds__(R >= 5 ? 320 : 576, 1) pass_kernel(const __grid_constant__ PassLaunch P) {
   pass_body<R, GenericProg<R, GEN>>(P);
 }
 
@@ -435,7 +436,7 @@ void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, v
   cudaStream_t s = (cudaStream_t)stream;
   const int k = L.pass.k;
   const int R = L.pass.R;
-  if (k - R > 8 || k > 13 || R < 1) fail(SF_EINVAL, "internal: bad tile shape");
+  if (k - R > 9 || k > 13 || R < 1) fail(SF_EINVAL, "internal: bad tile shape");
   (void)fuse_bits;
   (void)tile_bits;
   bool gen = false;  // does the pass need the general-gate variant?

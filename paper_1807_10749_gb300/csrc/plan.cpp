@@ -487,9 +487,9 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
   const int k = std::min(tile_bits, m);
   const int L = std::max(1, std::min(run_bits, k));
   // register bits: at most the fusion width, at least enough that a tile
-  // needs no more than 256 threads, and leave >= 2^min(5,k-1) threads per tile
+  // needs no more than 512 threads, and leave >= 2^min(5,k-1) threads per tile
   int R = std::max(1, std::min(fuse_bits, k - std::min(5, k - 1)));
-  R = std::min(MAX_R, std::max(R, k - 8));
+  R = std::min(MAX_R, std::max(R, k - 9));
   int res = 0;
   cd sigma = 1.0;
   bool first = true;
@@ -705,7 +705,7 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
               st.tg[t] = dp.gpos[lb];
               t++;
             }
-          if (t > 8) fail(SF_EINVAL, "internal: more than 256 threads per tile");
+          if (t > 9) fail(SF_EINVAL, "internal: more than 512 threads per tile");
         }
         st.op_begin = (int)pp.ops.size();
         if (!emit_stage_ops(st_ops, st, local_of, dp.gpos, pp)) {
@@ -766,9 +766,10 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
     int mB = __builtin_popcountll(bm), mA = n - mB;
     if (mA > 32 || mB > 32) fail(SF_EUNSUPPORTED, "a half of more than 32 qubits");
     if (mA < 1 || mB < 1) fail(SF_EINVAL, "empty half");
-    // two tile buffers of 2^13 complex64 (128 KiB) per SM: the pipelined
-    // pass kernel holds at most 13 tile bits
-    P->tile_bits = o.tile_bits > 0 ? std::min(o.tile_bits, 13) : 13;
+    // the pipelined pass kernel holds three tile buffers of 2^k complex64 in
+    // shared memory, so k <= 13; the default k = 12 (96 KiB per CTA) lets two
+    // CTAs, i.e. two independent copy/compute pipelines, share an SM
+    P->tile_bits = o.tile_bits > 0 ? std::min(o.tile_bits, 13) : 12;
     P->fuse_bits = o.fuse_bits > 0 ? std::min(o.fuse_bits, MAX_R) : 5;
     P->run_bits = o.run_bits > 0 ? std::min(o.run_bits, 8) : 3;
     if (P->tile_bits < 6) P->tile_bits = 6;

@@ -37,7 +37,7 @@ struct Request {
   sf_path_sel sel;
   size_t ws_bytes = 0;
   int64_t footprint = 0;
-  double terms[3] = {0, 0, 0};  // runtime-model features (Eq. t_tot)
+  double terms[4] = {0, 0, 0, 0};  // runtime-model features (Eq. t_tot)
   std::vector<double> out;
   int state = Q_QUEUED;
   int err_code = 0;
@@ -62,7 +62,7 @@ struct sf_server {
   std::vector<std::thread> workers;
   // runtime model: when set, admission prefers the shortest predicted request
   bool model = false;
-  double coeffs[3] = {0, 0, 0};
+  double coeffs[4] = {0, 0, 0, 0};
   double max_wait_s = 1.0;
 };
 
@@ -315,7 +315,7 @@ int sf_server_set_cost_model(sf_server* s, const double* coeffs, double max_wait
   std::lock_guard<std::mutex> lk(s->mu);
   s->model = coeffs != nullptr;
   if (coeffs)
-    for (int j = 0; j < 3; j++) {
+    for (int j = 0; j < 4; j++) {
       if (!(coeffs[j] >= 0)) sf::fail(SF_EINVAL, "model coefficients must be >= 0");
       s->coeffs[j] = coeffs[j];
     }

@@ -231,7 +231,7 @@ void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, 
 void exec_free_cache(void* cache);
 
 // Features of the runtime model (Section 8, Eq. t_tot) for a request.
-void cost_terms(const Plan& p, const sf_path_sel& s, int64_t n_a, double t[3]);
+void cost_terms(const Plan& p, const sf_path_sel& s, int64_t n_a, double t[4]);
 
 // Run-time specialised pass kernels (jit.cpp).
 void jit_prepare(Plan& p);

@@ -352,17 +352,17 @@ def fidelity_estimate(sums):
 
 
 def sf_plan_cost_terms(plan, sel, n_a):
-    """The three features (t0, t1, t2) of the runtime model for a request."""
-    t = (ctypes.c_double * 3)()
+    """The four features (1, t1, t2, t3) of the runtime model for a request."""
+    t = (ctypes.c_double * 4)()
     _check(lib().sf_plan_cost_terms(plan, ctypes.byref(sel), n_a, t))
     return np.array(t[:], dtype=np.float64)
 
 
 def sf_cost_fit(terms, seconds):
-    """Fit (C1, C1*C2, C3) >= 0 from an (n, 3) feature array and n times."""
+    """Fit (C0, C1, C1*C2, C3) >= 0 from an (n, 4) feature array and n times."""
     t = np.ascontiguousarray(terms, dtype=np.float64)
     s = np.ascontiguousarray(seconds, dtype=np.float64)
-    c = (ctypes.c_double * 3)()
+    c = (ctypes.c_double * 4)()
     _check(lib().sf_cost_fit(_ptr(t), _ptr(s), len(s), c))
     return np.array(c[:], dtype=np.float64)
 

@@ -165,27 +165,28 @@ def test_cost_terms_follow_eq_t_tot():
     n_a = 1000
     t = sfsim.sf_plan_cost_terms(p.handle, sfsim.selection("fraction", fidelity=0.25, seed=7), n_a)
     K = 64   # floor(0.25 * 2^8) prefixes of 2^7 paths
-    assert np.allclose(t, [K * work * dp, K * work * 128 * (d - dp), K * 128 * n_a], rtol=1e-12)
+    assert np.allclose(t, [1, K * work * dp, K * work * 128 * (d - dp), K * 128 * n_a], rtol=1e-12)
     # a range inside one prefix: one prefix, 10 paths
     t = sfsim.sf_plan_cost_terms(p.handle, sfsim.selection("range", first=300, count=10), n_a)
-    assert np.allclose(t, [work * dp, work * 128 * (d - dp), 10 * n_a], rtol=1e-12)
+    assert np.allclose(t, [1, work * dp, work * 128 * (d - dp), 10 * n_a], rtol=1e-12)
     # a range over a prefix boundary: two prefixes
     t = sfsim.sf_plan_cost_terms(p.handle, sfsim.selection("range", first=250, count=10), n_a)
-    assert np.isclose(t[0], 2 * work * dp)
+    assert np.isclose(t[1], 2 * work * dp)
     p.close()
 
 
 def test_cost_fit_recovers_coefficients():
     rng = np.random.default_rng(4)
-    T = rng.uniform(0.0, 1.0, size=(12, 3)) * np.array([1e9, 1e11, 1e8])
-    a = np.array([2e-12, 3e-14, 5e-10])
+    T = rng.uniform(0.0, 1.0, size=(12, 4)) * np.array([1, 1e9, 1e11, 1e8])
+    T[:, 0] = 1.0
+    a = np.array([1e-4, 2e-12, 3e-14, 5e-10])
     secs = T @ a
     got = sfsim.sf_cost_fit(T, secs)
     assert np.allclose(got, a, rtol=1e-8)
     assert abs(sfsim.sf_cost_predict(T[0], got) - secs[0]) <= 1e-9 * secs[0]
     # a coefficient that would come out negative is clipped to zero
-    secs2 = T[:, 0] * 2e-12 + T[:, 2] * 5e-10
+    secs2 = 1e-4 + T[:, 1] * 2e-12 + T[:, 3] * 5e-10
     got2 = sfsim.sf_cost_fit(T, secs2)
-    assert got2[1] == 0.0 and np.allclose(got2[[0, 2]], [2e-12, 5e-10], rtol=1e-8)
+    assert got2[2] == 0.0 and np.allclose(got2[[0, 1, 3]], [1e-4, 2e-12, 5e-10], rtol=1e-8)
     with pytest.raises(sfsim.SFError):
         sfsim.sf_cost_fit(T, -secs)

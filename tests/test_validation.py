@@ -54,19 +54,23 @@ def c2():
 @pytest.mark.parametrize("f", [1 / 4, 1 / 16, 1 / 64])
 def test_fidelity_estimate_tracks_f_actual(c2, f):
     """The exact Claimant against a Verifier that sums a random fraction f of
-    the paths: f_e within max(10%, 3/sqrt(K)) of f_actual (K selected paths;
-    a statistical check, Section 3 and Fig. 5), and within 0.02 of the
-    Verifier's own estimate 2^n E|v|^2."""
+    the paths (Section 3, Fig. 5; a statistical check): over three seeded
+    selections the mean of f_e / f_actual is within 10% of 1 and each one
+    within 25%; f_e is within 0.02 + 10% of the Verifier's own estimate
+    2^n E|v|^2 (Appendix C)."""
     plan, bits, exact = c2
-    ver, f_actual = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=f, seed=5))
-    K = f_actual * 2 ** 15
-    sums = _overlap(exact, ver)
-    np.testing.assert_allclose(sums, validation.overlap_sums(exact, ver), rtol=1e-10)
-    fe = sfsim.fidelity_estimate(sums)
-    f1 = 2.0 ** 30 * np.mean(np.abs(ver) ** 2)
-    print(f"f = {f}: f_e = {fe:.4f}, f_actual = {f_actual:.4f}, K = {K:.0f}")
-    assert abs(fe - f_actual) <= max(0.1, 3 / np.sqrt(K)) * f_actual, (fe, f_actual)
-    assert abs(fe - f1) <= 0.02 + 0.1 * f1, (fe, f1)
+    ratios = []
+    for seed in (5, 6, 7):
+        ver, f_actual = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=f, seed=seed))
+        sums = _overlap(exact, ver)
+        np.testing.assert_allclose(sums, validation.overlap_sums(exact, ver), rtol=1e-10)
+        fe = sfsim.fidelity_estimate(sums)
+        f1 = 2.0 ** 30 * np.mean(np.abs(ver) ** 2)
+        print(f"f = {f}, seed {seed}: f_e = {fe:.4f}, f1 = {f1:.4f}, f_actual = {f_actual:.4f}")
+        assert abs(fe - f1) <= 0.02 + 0.1 * f1, (fe, f1)
+        ratios.append(fe / f_actual)
+    assert abs(np.mean(ratios) - 1) <= 0.1, ratios
+    assert all(abs(r - 1) <= 0.25 for r in ratios), ratios
 
 
 def test_protocol_pass_and_fail(c2):
