@@ -138,7 +138,22 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     o << "const uint32_t pf = swz(" << deposit(st.tpos, k - R) << ");\n";
     o << "const uint32_t gfix = g.base | " << deposit(st.tg, k - R) << ";\n(void)gfix;\n";
     o << "float2 v[" << NR << "];\n";
-    for (int i = 0; i < NR; i++) o << "v[" << i << "] = sm[pf ^ " << C[i] << "u];\n";
+    // when tile bit 0 is a register bit, amplitudes i and i ^ (1 << j0) share
+    // a 16-byte chunk (swz keeps chunks whole): move them as one float4
+    int j0 = -1;
+    for (int j = 0; j < R; j++)
+      if (st.rbit[j] == 0) j0 = j;
+    if (j0 >= 0) {
+      o << "{ const float4* sm4 = reinterpret_cast<const float4*>(sm);\n";
+      for (int i = 0; i < NR; i++) {
+        if ((i >> j0) & 1) continue;
+        o << "{ const float4 q = sm4[(pf ^ " << C[i] << "u) >> 1]; v[" << i << "] = make_float2(q.x, q.y); v["
+          << (i | (1 << j0)) << "] = make_float2(q.z, q.w); }\n";
+      }
+      o << "}\n";
+    } else {
+      for (int i = 0; i < NR; i++) o << "v[" << i << "] = sm[pf ^ " << C[i] << "u];\n";
+    }
     bool kst = false;  // per-thread phase accumulated over the stage
     o << "int kst = 0;\n";
     for (int oi = st.op_begin; oi < st.op_end; oi++) {
@@ -280,7 +295,17 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
         << "; v[i].y *= " << flit(d.post_scale) << "; }\n";
     }
     o << "(void)kst;\n";
-    for (int i = 0; i < NR; i++) o << "sm[pf ^ " << C[i] << "u] = v[" << i << "];\n";
+    if (j0 >= 0) {
+      o << "{ float4* sm4 = reinterpret_cast<float4*>(sm);\n";
+      for (int i = 0; i < NR; i++) {
+        if ((i >> j0) & 1) continue;
+        o << "sm4[(pf ^ " << C[i] << "u) >> 1] = make_float4(v[" << i << "].x, v[" << i << "].y, v["
+          << (i | (1 << j0)) << "].x, v[" << (i | (1 << j0)) << "].y);\n";
+      }
+      o << "}\n";
+    } else {
+      for (int i = 0; i < NR; i++) o << "sm[pf ^ " << C[i] << "u] = v[" << i << "];\n";
+    }
     o << "compute_bar(ncomp);\n}\n";
   }
   o << "}\n};\n}  // namespace sf\n";
