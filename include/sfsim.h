@@ -109,7 +109,11 @@ typedef struct {
   int32_t jit;              /* 1 = compile every pass of the plan into a kernel of
                                its own at plan time (NVRTC; SF_EUNSUPPORTED where
                                NVRTC is missing), 0 = the generic pass kernel */
-  int32_t reserved[5];
+  int32_t split_last;       /* with the last level folded into the gather: 0 = plan
+                               the level before it and the last segment as one
+                               program (no node is written between them), 1 = two
+                               programs with the node in between */
+  int32_t reserved[4];
 } sf_plan_opts;
 
 SF_API void sf_plan_opts_default(sf_plan_opts* o);

@@ -214,7 +214,7 @@ int sf_plan_segment_stats(const sf_plan* h, int half, int segment, int* passes, 
   const int nL = (int)p.levels.size();
   const sf::SegmentPlan* seg = nullptr;
   if (segment >= 0 && segment <= nL) seg = &H.seg[segment];
-  else if (segment == nL + 1 && p.deferred) seg = &H.last_deferred;
+  else if (segment == nL + 1 && p.deferred) seg = p.merged_last ? &H.last_merged : &H.last_deferred;
   else sf::fail(SF_EINVAL, "segment out of range");
   if (passes) *passes = (int)seg->passes.size();
   if (stages) *stages = seg->n_stages;

@@ -55,8 +55,15 @@ struct Layout {
   size_t total_slots = 0;
 };
 
-Layout make_layout(const Plan& p, uint64_t n_finals, int64_t budget_override = 0) {
+// Depths whose nodes are cached: all levels, except that the finals of a
+// merged last program start from depth nL - 2.
+int cached_depths(const Plan& p) {
   const int nL = (int)p.levels.size();
+  return p.merged_last ? nL - 1 : nL;
+}
+
+Layout make_layout(const Plan& p, uint64_t n_finals, int64_t budget_override = 0) {
+  const int nL = cached_depths(p);
   const size_t nb = node_bytes(p);
   int64_t budget = budget_override > 0 ? budget_override : p.opts.hbm_budget_bytes;
   const size_t amps = ((size_t)1 << p.A.m) + ((size_t)1 << p.B.m);
@@ -298,9 +305,16 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   auto bufA = [&](size_t slot) { return (void*)(base + slot * nb); };
   auto bufB = [&](size_t slot) { return (void*)(base + slot * nb + bytesA); };
   const int fb = plan.deferred ? plan.defer_bits : 0;
-  const int sh_f = plan.deferred ? 0 : (nL > 0 ? plan.levels[nL - 1].bits : 0);
-  const SegmentPlan& finA = plan.deferred ? plan.A.last_deferred : plan.A.seg[nL];
-  const SegmentPlan& finB = plan.deferred ? plan.B.last_deferred : plan.B.seg[nL];
+  // nc cached depths 0 .. nc-1; a final's parent is its node at depth nc-1,
+  // sh_f path bits (of the final id) above it
+  const int nc = cached_depths(plan);
+  int sh_f = 0;
+  if (plan.merged_last) sh_f = nL >= 2 ? plan.levels[nL - 2].bits : 0;
+  else if (!plan.deferred) sh_f = nL > 0 ? plan.levels[nL - 1].bits : 0;
+  const SegmentPlan& finA =
+      plan.merged_last ? plan.A.last_merged : (plan.deferred ? plan.A.last_deferred : plan.A.seg[nL]);
+  const SegmentPlan& finB =
+      plan.merged_last ? plan.B.last_merged : (plan.deferred ? plan.B.last_deferred : plan.B.seg[nL]);
 
   // gather template
   GatherLaunch G;
@@ -385,16 +399,15 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         block.push_back(f);
         more = next_final(f);
       }
-      // parents at depth nL-1 (ids) of the block's finals
+      // parents at depth nc-1 (ids) of the block's finals
       std::vector<uint64_t> pid(block.size());
       for (size_t i = 0; i < block.size(); i++) pid[i] = block[i].fid >> sh_f;
-      // cached depths 0 .. nL-1
-      std::vector<size_t> slot_of_final_parent(block.size(), 0);
+      // cached depths 0 .. nc-1
       std::vector<int> prev_slot;  // slot index (within depth) per needed node at depth s-1
       std::vector<uint64_t> prev_ids;
-      for (int s = 0; s < nL; s++) {
-        const int below = total_bits_below(plan, s) - (nL > 0 ? plan.levels[nL - 1].bits : 0);
-        // node id at depth s = pid >> (bits of levels s .. nL-2)
+      for (int s = 0; s < nc; s++) {
+        const int below = total_bits_below(plan, s) - (nc > 0 ? total_bits_below(plan, nc - 1) : 0);
+        // node id at depth s = pid >> (bits of levels s .. nc-2)
         std::vector<uint64_t> ids;
         for (uint64_t v : pid) {
           uint64_t id = below >= 64 ? 0 : (v >> below);
@@ -468,15 +481,15 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         const void *inA = nullptr, *inB = nullptr;
         bool pdead = false;
         cd psa = plan.A.root_scale, psb = plan.B.root_scale;
-        if (nL > 0) {
+        if (nc > 0) {
           size_t pi = std::lower_bound(prev_ids.begin(), prev_ids.end(), pid[i]) - prev_ids.begin();
           if (pi >= prev_ids.size() || prev_ids[pi] != pid[i]) fail(SF_EINVAL, "internal: final parent missing");
-          const Slot& ps = C->slots[nL - 1][prev_slot[pi]];
+          const Slot& ps = C->slots[nc - 1][prev_slot[pi]];
           pdead = ps.dead;
           psa = ps.sa;
           psb = ps.sb;
-          inA = bufA(C->first_slot[nL - 1] + prev_slot[pi]);
-          inB = bufB(C->first_slot[nL - 1] + prev_slot[pi]);
+          inA = bufA(C->first_slot[nc - 1] + prev_slot[pi]);
+          inB = bufB(C->first_slot[nc - 1] + prev_slot[pi]);
         }
         bool dead = pdead || dead_by_pins(finA.passes[0].dev, plan, fpath) ||
                     dead_by_pins(finB.passes[0].dev, plan, fpath);
@@ -502,7 +515,7 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         // the plain form shares nothing below the selection prefix: every
         // path re-evolves its levels under the prefix checkpoint
         int cum = 0;
-        for (int s = 0; s < nL; s++) {
+        for (int s = 0; s < nc; s++) {
           if (cum > plan.xs)
             for (auto& sl : C->slots[s]) sl.valid = false;
           cum += plan.levels[s].bits;

@@ -399,6 +399,7 @@ void jit_prepare(Plan& p) {
     for (auto& s : h->seg)
       for (auto& pp : s.passes) all.push_back(&pp);
     for (auto& pp : h->last_deferred.passes) all.push_back(&pp);
+    for (auto& pp : h->last_merged.passes) all.push_back(&pp);
   }
   std::vector<Entry*> todo;
   p.jit_entries.clear();

@@ -1014,7 +1014,17 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
         plan_segment(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, P->tile_bits, P->fuse_bits, P->run_bits,
                      H.last_deferred);
         H.last_deferred.scale *= seg_global[2 * nL + side];
+        if (!o.split_last) {
+          // no branching happens at the folded level, so the segment that
+          // leads to it and the last segment run as one program per final
+          std::vector<HOp> ops = H.seg_ops[nL - 1];
+          ops.insert(ops.end(), H.seg_ops[nL + 1].begin(), H.seg_ops[nL + 1].end());
+          std::vector<Pin> pin_m = nL >= 2 ? H.seg[nL - 2].pins_out : H.root_pins;
+          plan_segment(H.m, ops, pin_m, nL == 1, P->tile_bits, P->fuse_bits, P->run_bits, H.last_merged);
+          H.last_merged.scale *= seg_global[2 * (nL - 1) + side] * seg_global[2 * nL + side];
+        }
       }
+      P->merged_last = P->deferred && !o.split_last;
       // gather byte tables: bitstring byte -> layout index bits (deferred
       // positions excluded; the gather adds them)
       H.tab.assign(8 * 256, 0);
@@ -1072,9 +1082,14 @@ std::string plan_describe(const Plan& p) {
     const HalfPlan& H = side ? p.B : p.A;
     const int nseg = (int)H.seg.size() + (p.deferred ? 1 : 0);
     for (int s = 0; s < nseg; s++) {
-      const SegmentPlan& sp = s < (int)H.seg.size() ? H.seg[s] : H.last_deferred;
+      const bool fin = s == (int)H.seg.size();
+      if (p.merged_last && s == (int)H.seg.size() - 2) continue;  // runs inside the merged program
+      const SegmentPlan& sp = !fin ? H.seg[s] : (p.merged_last ? H.last_merged : H.last_deferred);
       snprintf(b, sizeof b, "half %c segment %d%s: %zu passes\n", side ? 'B' : 'A', s,
-               s == (int)H.seg.size() ? " (folded last level)" : "", sp.passes.size());
+               fin ? (p.merged_last ? " (the level before the folded last level, and the last segment)"
+                                    : " (folded last level)")
+                   : "",
+               sp.passes.size());
       o += b;
       for (size_t q = 0; q < sp.passes.size(); q++) {
         const PassPlan& pp = sp.passes[q];

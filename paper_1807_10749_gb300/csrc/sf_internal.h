@@ -136,6 +136,7 @@ struct HalfPlan {
   cd root_scale = 1.0;
   std::vector<SegmentPlan> seg;          // per segment, full program
   SegmentPlan last_deferred;             // last segment without deferred ops
+  SegmentPlan last_merged;               // the level before it and last_deferred as one program
   std::vector<uint32_t> tab;             // 8 x 256 gather byte tables
 };
 
@@ -183,6 +184,7 @@ struct Plan {
   int xs = 0;  // FRACTION prefix bits
   HalfPlan A, B;
   bool deferred = false;       // last level folded into the gather
+  bool merged_last = false;    // finals run last_merged from depth nL - 2 (no depth nL - 1 nodes)
   int defer_bits = 0;          // bits of the last level when deferred
   float ma[MAX_DEFER][4][8];
   float mb[MAX_DEFER][4][8];

@@ -50,7 +50,7 @@ class sf_plan_opts(ctypes.Structure):
                 ("fuse_bits", ctypes.c_int32), ("exec_mode", ctypes.c_int32),
                 ("defer_last_level", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("batch_paths", ctypes.c_int32), ("run_bits", ctypes.c_int32),
-                ("jit", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("jit", ctypes.c_int32), ("split_last", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class sf_path_sel(ctypes.Structure):

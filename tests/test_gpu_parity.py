@@ -187,8 +187,8 @@ def test_5x6_full_sum_porter_thomas(jit):
 
 
 # ---------------------------------------------------------------- 6x7 (C3)
-@pytest.mark.parametrize("kind", ["cz", "haar"])
-def test_6x7_path_list_matches_oracle(kind, jit):
+@pytest.mark.parametrize("kind,split", [("cz", 0), ("cz", 1), ("haar", 0)])
+def test_6x7_path_list_matches_oracle(kind, split, jit):
     w, text = workload("6x7_d26", haar=(kind == "haar"))
     c = ocirc.parse(text)
     setup = sim.SFSetup(c, w["side_b_mask"])
@@ -201,9 +201,11 @@ def test_6x7_path_list_matches_oracle(kind, jit):
     if kind == "haar":
         ids = np.unique(np.concatenate([ids[:6], full[:40]]))
     ref = sim.sf_amplitudes(setup, ids, bits)
-    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
+    # split = 0: the level before the folded last level runs inside the last
+    # program; split = 1: as its own segment with the node in between
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], split_last=split)
     amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
-    check_close(amp, ref, 42, f"6x7 {kind} {len(ids)} paths")
+    check_close(amp, ref, 42, f"6x7 {kind} split={split} {len(ids)} paths")
     p.close()
 
 
