@@ -289,6 +289,8 @@ def main():
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--fuse-bits", type=int, default=0)
     ap.add_argument("--run-bits", type=int, default=0)
+    ap.add_argument("--split-last", type=int, default=0, choices=[0, 1],
+                    help="1: run the level before the folded last level as its own segment")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1],
                     help="1: per-pass specialised kernels compiled at plan time; 0: the generic pass kernel")
     args = ap.parse_args()
@@ -321,7 +323,8 @@ def main():
     mode = sfsim.SF_EXEC_PLAIN if args.exec_mode == "plain" else sfsim.SF_EXEC_BATCHED
     t_plan = time.perf_counter()
     plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode, tile_bits=args.tile_bits,
-                      fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit)
+                      fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit,
+                      split_last=args.split_last)
     t_plan = time.perf_counter() - t_plan
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
@@ -424,8 +427,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
                                               "tile_bits": args.tile_bits or 12, "fuse_bits": args.fuse_bits or 5,
-                                              "run_bits": args.run_bits or 3,
+                                              "run_bits": args.run_bits or 4,
                                               "pass_kernels": "specialised" if args.jit else "generic",
+                                              "split_last": args.split_last,
                                               "plan_seconds": t_plan,
                                               "paths_selected": n_sel, "parallelism": f"paths x{world}",
                                               "wall_s": wall}),

@@ -105,7 +105,7 @@ typedef struct {
                                 free memory at plan time */
   int32_t batch_paths;       /* max leaf groups per launch, 0 = from budget */
   int32_t run_bits;          /* log2 contiguous amplitudes per copy run (the
-                                index bits every pass keeps active), 0 = 3 */
+                                index bits every pass keeps active), 0 = 4 */
   int32_t jit;              /* 1 = compile every pass of the plan into a kernel of
                                its own at plan time (NVRTC; SF_EUNSUPPORTED where
                                NVRTC is missing), 0 = the generic pass kernel */
@@ -164,8 +164,9 @@ typedef struct {
   int64_t n_list;
 } sf_path_sel;
 
-/* Autotuner: plans the circuit with every candidate (tile_bits in {12, 13},
- * fuse_bits in {4, 5}, run_bits in {3, 4, 5}) on top of *base, runs the first
+/* Autotuner: plans the circuit with every candidate (tile_bits in {11, 12, 13},
+ * fuse_bits in {4, 5}, run_bits in {3, 4, 5}) on top of *base (with base->jit
+ * set, each candidate's specialised kernels are compiled first), runs the first
  * sample_paths paths of *sel for the n device bitstrings d_bits once to warm
  * up and once timed (CUDA events, a private stream), and writes the fastest
  * candidate's options to *best and its time to *best_seconds (may be NULL).

@@ -771,7 +771,7 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
     // CTAs, i.e. two independent copy/compute pipelines, share an SM
     P->tile_bits = o.tile_bits > 0 ? std::min(o.tile_bits, 13) : 12;
     P->fuse_bits = o.fuse_bits > 0 ? std::min(o.fuse_bits, MAX_R) : 5;
-    P->run_bits = o.run_bits > 0 ? std::min(o.run_bits, 8) : 3;
+    P->run_bits = o.run_bits > 0 ? std::min(o.run_bits, 8) : 4;
     if (P->tile_bits < 6) P->tile_bits = 6;
 
     // cross gates in time order (cycle, lower qubit, higher qubit)

@@ -53,7 +53,7 @@ extern "C" int sf_plan_autotune(const sf_circuit* c, const sf_plan_opts* base, c
     ok(cudaEventCreate(&e1), "cudaEventCreate");
     double best_t = 1e300;
     sf_plan_opts best_o = b;
-    for (int tb : {12, 13})
+    for (int tb : {11, 12, 13})
       for (int fb : {4, 5})
         for (int rb : {3, 4, 5}) {
           sf_plan_opts o = b;
@@ -66,6 +66,7 @@ extern "C" int sf_plan_autotune(const sf_circuit* c, const sf_plan_opts* base, c
           } catch (const sf::Error&) {
             continue;  // not a valid shape for this circuit
           }
+          if (o.jit) sf::jit_prepare(*P);  // time the kernels the plan will run
           sf::ensure_device(*P);
           DevBuf ws;
           const size_t need = sf::exec_workspace_bytes(*P, n, s);

@@ -101,7 +101,7 @@ def test_server_admits_shortest_predicted_first():
     b_long = inputs.random_bitstrings(42, 2000, 1)
     b_big = inputs.random_bitstrings(30, 100_000, 2)
     b_small = inputs.random_bitstrings(16, 100, 3)
-    s_long = sfsim.selection("range", first=0, count=1 << 14)
+    s_long = sfsim.selection("fraction", fidelity=1.0)   # all 2^25 paths: seconds of work
     s_all = sfsim.selection("fraction", fidelity=1.0)
     order = {}
     for use_model in (False, True):
@@ -113,9 +113,12 @@ def test_server_admits_shortest_predicted_first():
             time.sleep(0.3)      # the long request is running
             tb = sfsim.sf_server_submit(srv, big.handle, b_big, s_all)
             ts = sfsim.sf_server_submit(srv, small.handle, b_small, s_all)
+            sfsim.sf_server_cancel(srv, t0)   # frees the worker with both queued
             qb = _times_when_done(srv, tb)[0]
             qs = _times_when_done(srv, ts)[0]
-            for t, n in ((t0, len(b_long)), (tb, len(b_big)), (ts, len(b_small))):
+            with pytest.raises(sfsim.SFError):
+                sfsim.sf_server_wait(srv, t0, len(b_long))
+            for t, n in ((tb, len(b_big)), (ts, len(b_small))):
                 sfsim.sf_server_wait(srv, t, n)
             order[use_model] = (qb, qs)
         finally:
