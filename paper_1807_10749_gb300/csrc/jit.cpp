@@ -138,21 +138,36 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     o << "const uint32_t pf = swz(" << deposit(st.tpos, k - R) << ");\n";
     o << "const uint32_t gfix = g.base | " << deposit(st.tg, k - R) << ";\n(void)gfix;\n";
     o << "float2 v[" << NR << "];\n";
+    // Addresses pf ^ C_i: the swizzle only touches bits 1..3, so with
+    // pf = ph | pl and C_i = h_i | l_i split at bit 4, pf ^ C_i =
+    // (ph | (pl ^ l_i)) + h_i. One base pointer per distinct low part l, and a
+    // constant offset h_i per access.
+    uint32_t lows[32];
+    int nlow = 0;
+    auto low_id = [&](uint32_t l) {
+      for (int q = 0; q < nlow; q++)
+        if (lows[q] == l) return q;
+      lows[nlow] = l;
+      return nlow++;
+    };
+    int lid[32];
+    for (int i = 0; i < NR; i++) lid[i] = low_id(C[i] & 0xFu);
+    o << "const uint32_t ph = pf & ~0xFu, pl = pf & 0xFu;\n";
+    for (int q = 0; q < nlow; q++) o << "float2* const sb" << q << " = sm + (ph | (pl ^ " << lows[q] << "u));\n";
+    auto at = [&](int i) { return "sb" + std::to_string(lid[i]) + " + " + std::to_string(C[i] & ~0xFu) + "u"; };
     // when tile bit 0 is a register bit, amplitudes i and i ^ (1 << j0) share
     // a 16-byte chunk (swz keeps chunks whole): move them as one float4
     int j0 = -1;
     for (int j = 0; j < R; j++)
       if (st.rbit[j] == 0) j0 = j;
     if (j0 >= 0) {
-      o << "{ const float4* sm4 = reinterpret_cast<const float4*>(sm);\n";
       for (int i = 0; i < NR; i++) {
         if ((i >> j0) & 1) continue;
-        o << "{ const float4 q = sm4[(pf ^ " << C[i] << "u) >> 1]; v[" << i << "] = make_float2(q.x, q.y); v["
-          << (i | (1 << j0)) << "] = make_float2(q.z, q.w); }\n";
+        o << "{ const float4 q = *reinterpret_cast<const float4*>(" << at(i) << "); v[" << i
+          << "] = make_float2(q.x, q.y); v[" << (i | (1 << j0)) << "] = make_float2(q.z, q.w); }\n";
       }
-      o << "}\n";
     } else {
-      for (int i = 0; i < NR; i++) o << "v[" << i << "] = sm[pf ^ " << C[i] << "u];\n";
+      for (int i = 0; i < NR; i++) o << "v[" << i << "] = *(" << at(i) << ");\n";
     }
     bool kst = false;  // per-thread phase accumulated over the stage
     o << "int kst = 0;\n";
@@ -296,15 +311,13 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     }
     o << "(void)kst;\n";
     if (j0 >= 0) {
-      o << "{ float4* sm4 = reinterpret_cast<float4*>(sm);\n";
       for (int i = 0; i < NR; i++) {
         if ((i >> j0) & 1) continue;
-        o << "sm4[(pf ^ " << C[i] << "u) >> 1] = make_float4(v[" << i << "].x, v[" << i << "].y, v["
+        o << "*reinterpret_cast<float4*>(" << at(i) << ") = make_float4(v[" << i << "].x, v[" << i << "].y, v["
           << (i | (1 << j0)) << "].x, v[" << (i | (1 << j0)) << "].y);\n";
       }
-      o << "}\n";
     } else {
-      for (int i = 0; i < NR; i++) o << "sm[pf ^ " << C[i] << "u] = v[" << i << "];\n";
+      for (int i = 0; i < NR; i++) o << "*(" << at(i) << ") = v[" << i << "];\n";
     }
     o << "compute_bar(ncomp);\n}\n";
   }
