@@ -112,16 +112,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n_nodes_bytes_per_launch):
-    """DRAM bytes per pass launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+def ncu_traffic(alg_bytes_per_launch):
+    """DRAM bytes per pass launch: the DRAM-to-algorithmic byte ratio of the
+    committed ncu capture (a smaller case of the same kernel) times this
+    workload's algorithmic bytes per launch, if the capture was taken on the
+    current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "pass_kernel_7x8_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
         if d.get("pass_sources_sha256_16") != kernel_source_hash():
             return None
-        return float(d["dram_bytes_per_launch"])
+        return float(d["dram_bytes_per_algorithmic_byte"]) * alg_bytes_per_launch
     except Exception:
         return None
 

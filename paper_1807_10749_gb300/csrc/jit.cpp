@@ -416,10 +416,18 @@ void jit_prepare(Plan& p) {
   }
   std::vector<Entry*> todo;
   p.jit_entries.clear();
+  const char* dump = std::getenv("SF_JIT_DUMP");  // directory for the generated sources
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (PassPlan* pp : all) {
       std::string src = gen_pass(*pp, kKernelName);
+      if (dump) {
+        const std::string fn = std::string(dump) + "/pass_" + std::to_string(p.jit_entries.size()) + ".cu";
+        if (FILE* f = std::fopen(fn.c_str(), "w")) {
+          std::fputs(src.c_str(), f);
+          std::fclose(f);
+        }
+      }
       auto& slot = cache()[src];
       if (!slot) {
         slot = std::make_unique<Entry>();
