@@ -112,6 +112,87 @@ std::string deposit(const int8_t* pos, int nbits) {
   return e.empty() ? "0u" : e;
 }
 
+// The tile copies of one pass with its geometry as constants. Lane l moves
+// chunks c = l + 32 j (elements 2c, 2c+1). The global offset of a chunk is
+// the deposit of its tile bits into the pass's index positions, a lane part
+// plus a constant per j. Its shared-memory slot swz(2c) is
+// (swz(2l) ^ lo_j) | 64 j, with lo_j the swizzle's bits 1..3 for the j part:
+// one base per distinct lo_j plus a constant. Runs with a pinned bit other
+// than the tile's value are skipped (structural zeros).
+void gen_copy(std::ostringstream& o, const PassPlan& pp) {
+  const DevPass& d = pp.dev;
+  if (d.k < 6) {  // fewer chunks than lanes: the generic loops
+    o << "static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, "
+         "int lane, const CopyCtx& cc) { GenericCopy::load_tile(P, g, dst, lane, cc); }\n"
+      << "static __device__ __forceinline__ void store_tile(const PassLaunch& P, const ItemGeo& g, "
+         "const float2* buf, int lane, const CopyCtx& cc) { GenericCopy::store_tile(P, g, buf, lane, cc); }\n";
+    return;
+  }
+  const int k = d.k, L = d.L, nj = 1 << (k - 6);
+  int8_t lpos[5];
+  for (int t = 0; t < 5; t++) lpos[t] = d.gpos[t + 1];
+  auto pin_mask = [&](const DevPin* pins, int n) {
+    uint32_t m = 0;
+    for (int i = 0; i < n; i++)
+      for (int j = 0; j < k; j++)
+        if (d.gpos[j] == pins[i].pos) m |= 1u << j;
+    return m >> L;  // pins inside a run are zero-filled by the stage warps
+  };
+  const uint32_t rm_in = pin_mask(d.pin_in, d.n_pin_in), rm_out = pin_mask(d.pin_out, d.n_pin_out);
+  uint32_t G[1 << 8], lo[1 << 8], rj[1 << 8];
+  uint32_t lows[8];
+  int nlow = 0, lid[1 << 8];
+  for (int j = 0; j < nj; j++) {
+    const uint32_t e = 64u * (uint32_t)j;
+    uint32_t g = 0;
+    for (int b = 6; b < k; b++)
+      if ((e >> b) & 1) g |= 1u << d.gpos[b];
+    G[j] = g;
+    lo[j] = swz(e) & 0xFu;
+    rj[j] = e >> L;
+    int q = 0;
+    while (q < nlow && lows[q] != lo[j]) q++;
+    if (q == nlow) lows[nlow++] = lo[j];
+    lid[j] = q;
+  }
+  std::string gl = deposit(lpos, 5);
+  for (size_t at; (at = gl.find("tid")) != std::string::npos;) gl.replace(at, 3, "ln");
+  // loads
+  o << "static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, "
+       "int lane, const CopyCtx&) {\n"
+    << "const uint32_t ln = (uint32_t)lane;\n"
+    << "const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in) + (g.base | " << gl << ");\n"
+    << "const uint32_t s2 = swz(2u * ln);\n";
+  for (int q = 0; q < nlow; q++) o << "const uint32_t d" << q << " = dst + 8u * (s2 ^ " << lows[q] << "u);\n";
+  if (rm_in) o << "const uint32_t rl = ((2u * ln) >> " << L << ") & " << rm_in << "u, rv = g.lin_v >> " << L << ";\n";
+  for (int j = 0; j < nj; j++) {
+    if (rm_in) o << "if ((rl | " << (rj[j] & rm_in) << "u) == rv) ";
+    o << "cp_async16(d" << lid[j] << " + " << 512u * j << "u, in + " << G[j] << "u);\n";
+  }
+  o << "}\n";
+  // stores, eight chunks in flight per lane
+  o << "static __device__ __forceinline__ void store_tile(const PassLaunch& P, const ItemGeo& g, const float2* buf, "
+       "int lane, const CopyCtx&) {\n"
+    << "const uint32_t ln = (uint32_t)lane;\n"
+    << "float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out) + (g.base | " << gl << ");\n"
+    << "const uint32_t s2 = swz(2u * ln);\n";
+  for (int q = 0; q < nlow; q++)
+    o << "const float4* b" << q << " = reinterpret_cast<const float4*>(buf + (s2 ^ " << lows[q] << "u));\n";
+  if (rm_out)
+    o << "const uint32_t rl = ((2u * ln) >> " << L << ") & " << rm_out << "u, rv = g.lout_v >> " << L << ";\n";
+  for (int j0 = 0; j0 < nj; j0 += 8) {
+    o << "{\n";
+    for (int j = j0; j < std::min(nj, j0 + 8); j++)
+      o << "const float4 q" << j - j0 << " = b" << lid[j] << "[" << 32u * j << "u];\n";
+    for (int j = j0; j < std::min(nj, j0 + 8); j++) {
+      if (rm_out) o << "if ((rl | " << (rj[j] & rm_out) << "u) == rv) ";
+      o << "*reinterpret_cast<float4*>(out + " << G[j] << "u) = q" << j - j0 << ";\n";
+    }
+    o << "}\n";
+  }
+  o << "}\n";
+}
+
 // One pass as a stage program: struct `name`_prog in namespace sf and an
 // extern "C" kernel `name`.
 std::string gen_pass(const PassPlan& pp, const std::string& name) {
@@ -321,9 +402,14 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     }
     o << "compute_bar(ncomp);\n}\n";
   }
-  o << "}\n};\n}  // namespace sf\n";
+  o << "}\n";
+  gen_copy(o, pp);
+  o << "};\n}  // namespace sf\n";
   const int threads = (((1 << (k - R)) + 31) / 32) * 32 + 64;  // stage warps + the two copy warps
-  o << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", 1) " << name
+  // tiles of up to 2^12 amplitudes leave shared memory for two CTAs per SM:
+  // ask for the registers to allow it as well
+  const int min_blocks = k <= 12 ? 2 : 1;
+  o << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", " << min_blocks << ") " << name
     << "(const __grid_constant__ sf::PassLaunch P) {\n  sf::pass_body<" << R << ", sf::" << name
     << "_prog>(P);\n}\n";
   return o.str();

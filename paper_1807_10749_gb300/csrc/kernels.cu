@@ -222,7 +222,7 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
 // The generic stage program: reads the pass's stages, ops and phase groups
 // from the launch record and dispatches on them.
 template <int R, bool GEN>
-struct GenericProg {
+struct GenericProg : GenericCopy {
   static __device__ __forceinline__ void run(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
                                              int ncomp) {
     run_stages<R, GEN>(P, sm, g, w8, ncomp);

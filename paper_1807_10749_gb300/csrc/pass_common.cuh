@@ -223,8 +223,65 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
 // on empty[b], then frees the buffer (free[b]). Input-pinned (structurally
 // zero) runs are never read and output-pinned runs never written. Every wait
 // is bounded; a timeout sets the error flag and ends the kernel.
+// Copy geometry of a tile: run r (2^L contiguous amplitudes) of a tile sits
+// at global offset runoff[r]; chunk c (elements 2c, 2c+1) at swz(2c).
+struct CopyCtx {
+  const uint32_t* runoff;
+  int L, nchunk;
+  uint32_t lmask;
+};
+
+// The generic copy loops: four 16-byte chunks in flight per lane.
+struct GenericCopy {
+  static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, int lane,
+                                                   const CopyCtx& cc) {
+    const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
+    const uint32_t rm = g.lin_m >> cc.L, rv = g.lin_v >> cc.L;
+    for (int c0 = lane; c0 < cc.nchunk; c0 += 128) {
+      uint32_t so[4];
+      const float2* src[4];
+      bool ok[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int c = c0 + 32 * u;
+        const int e = c << 1, r = e >> cc.L;
+        ok[u] = c < cc.nchunk && (((uint32_t)r & rm) == rv);
+        so[u] = swz((uint32_t)e) * 8u;
+        src[u] = in + (g.base | cc.runoff[ok[u] ? r : 0] | (uint32_t)(e & cc.lmask));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (ok[u]) cp_async16(dst + so[u], src[u]);
+    }
+  }
+  static __device__ __forceinline__ void store_tile(const PassLaunch& P, const ItemGeo& g, const float2* buf,
+                                                    int lane, const CopyCtx& cc) {
+    float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
+    const float4* srcb = reinterpret_cast<const float4*>(buf);
+    const uint32_t rm = g.lout_m >> cc.L, rv = g.lout_v >> cc.L;
+    for (int c0 = lane; c0 < cc.nchunk; c0 += 128) {
+      float4 v[4];
+      float2* dst[4];
+      bool ok[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int c = c0 + 32 * u;
+        const int e = c << 1, r = e >> cc.L;
+        ok[u] = c < cc.nchunk && (((uint32_t)r & rm) == rv);
+        v[u] = srcb[swz((uint32_t)(ok[u] ? e : 0)) >> 1];
+        dst[u] = out + (g.base | cc.runoff[ok[u] ? r : 0] | (uint32_t)(e & cc.lmask));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        if (ok[u]) *reinterpret_cast<float4*>(dst[u]) = v[u];
+    }
+  }
+};
+
 // Prog::run(P, sm, g, w8, ncomp) runs the register stages of one tile (the
 // threads below 2^(k-R)); the other compute threads only join its barriers.
+// Prog::load_tile / Prog::store_tile move a tile between its node buffer and
+// shared memory (load warp: cp.async into dst; store warp: vector stores).
 template <int R, class Prog>
 __device__ __forceinline__ void pass_body(const PassLaunch& P) {
   constexpr int NBUF = 3;
@@ -262,6 +319,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
     for (int j = L; j < k; j++) hi |= (uint32_t)((rI >> (j - L)) & 1) << d.gpos[j];
     runoff[rI] = hi;
   }
+  const CopyCtx cc{runoff, L, nchunk, (uint32_t)lmask};
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int b = 0; b < NBUF; b++) {
@@ -291,27 +349,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
       if (*(volatile int*)&abort_flag) break;
       const ItemGeo g = item_geo(P, it, tiles_log2);
       if (lane == 0) geo[b] = g;
-      if (!d.gen_input) {
-        const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
-        const uint32_t dst = smem_u32(bufs + b * ntile);
-        const uint32_t rm = g.lin_m >> L, rv = g.lin_v >> L;
-        for (int c0 = lane; c0 < nchunk; c0 += 128) {
-          uint32_t so[4];
-          const float2* src[4];
-          bool ok[4];
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            const int c = c0 + 32 * u;
-            const int e = c << 1, r = e >> L;
-            ok[u] = c < nchunk && (((uint32_t)r & rm) == rv);
-            so[u] = swz((uint32_t)e) * 8u;
-            src[u] = in + (g.base | runoff[ok[u] ? r : 0] | (uint32_t)(e & lmask));
-          }
-#pragma unroll
-          for (int u = 0; u < 4; u++)
-            if (ok[u]) cp_async16(dst + so[u], src[u]);
-        }
-      }
+      if (!d.gen_input) Prog::load_tile(P, g, smem_u32(bufs + b * ntile), lane, cc);
       cp_async_arrive(smem_u32(&full[b]));
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&full[b]));
@@ -332,25 +370,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         break;
       }
       const ItemGeo g = geo[b];
-      float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
-      const float4* srcb = reinterpret_cast<const float4*>(bufs + b * ntile);
-      const uint32_t rm = g.lout_m >> L, rv = g.lout_v >> L;
-      for (int c0 = lane; c0 < nchunk; c0 += 128) {
-        float4 v[4];
-        float2* dst[4];
-        bool ok[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int c = c0 + 32 * u;
-          const int e = c << 1, r = e >> L;
-          ok[u] = c < nchunk && (((uint32_t)r & rm) == rv);
-          v[u] = srcb[swz((uint32_t)(ok[u] ? e : 0)) >> 1];
-          dst[u] = out + (g.base | runoff[ok[u] ? r : 0] | (uint32_t)(e & lmask));
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++)
-          if (ok[u]) *reinterpret_cast<float4*>(dst[u]) = v[u];
-      }
+      Prog::store_tile(P, g, bufs + b * ntile, lane, cc);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&freeb[b]));
     }

@@ -104,6 +104,19 @@ def test_4x4_four_way_branching(kind, dec, jit):
     p.close()
 
 
+def test_tiny_halves_all_paths(jit):
+    """Halves of 4 and 6 qubits: tiles smaller than one copy warp's 32 chunks."""
+    for (R, C, cut) in [(2, 4, 2), (3, 4, 2)]:
+        text = inputs.google_circuit(R, C, 14, 2).text()
+        n = R * C
+        c = ocirc.parse(text)
+        xs = np.arange(1 << n, dtype=np.uint64)
+        p = sfsim.Plan(text, jit=jit, side_b_mask=inputs.column_cut_mask(R, C, cut))
+        amp, _ = p.amplitudes(xs, sfsim.selection("fraction", fidelity=1.0))
+        check_close(amp, sim.sv_amplitudes(c, xs), n, f"{R}x{C} all paths")
+        p.close()
+
+
 def test_4x4_plain_equals_batched(jit):
     w, text = workload("4x4_d10")
     bits = inputs.random_bitstrings(16, 1024, w["bitstring_seed"])
