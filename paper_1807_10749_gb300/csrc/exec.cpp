@@ -139,6 +139,18 @@ bool dead_by_pins(const DevPass& dp, const Plan& p, uint64_t path) {
   return false;
 }
 
+// The live part of a pass's input a node reads: its pins' values (bit i =
+// value of input pin i). Nodes with one input buffer and equal keys read the
+// same amplitudes.
+uint64_t pin_key(const DevPass& dp, const Plan& p, uint64_t path) {
+  uint64_t k = 0;
+  for (int i = 0; i < dp.n_pin_in && i < 64; i++) {
+    Pin a{dp.pin_in[i].pos, dp.pin_in[i].xi, {dp.pin_in[i].v[0], dp.pin_in[i].v[1], dp.pin_in[i].v[2], dp.pin_in[i].v[3]}};
+    if (resolve(a, p, path)) k |= 1ull << i;
+  }
+  return k;
+}
+
 struct Job {
   const void* in;  // parent buffer (half base) or nullptr for generated input
   void* out;
@@ -146,8 +158,9 @@ struct Job {
 };
 
 // Algorithmic bytes of one pass launch: live input amplitudes read (unless
-// generated) plus live output amplitudes written, 8 bytes each, per node.
-double pass_bytes(const DevPass& d, int nodes) {
+// generated) once per distinct input buffer, plus live output amplitudes
+// written per node, 8 bytes each.
+double pass_bytes(const DevPass& d, int nodes, int inputs) {
   uint32_t active = 0;
   for (int j = 0; j < d.k; j++) active |= 1u << d.gpos[j];
   uint32_t pin_in = 0, pin_out = 0;
@@ -156,7 +169,7 @@ double pass_bytes(const DevPass& d, int nodes) {
   const double tiles = std::ldexp(1.0, d.n_free);
   const double rd = d.gen_input ? 0.0 : tiles * std::ldexp(1.0, d.k - __builtin_popcount(pin_in & active));
   const double wr = tiles * std::ldexp(1.0, d.k - __builtin_popcount(pin_out & active));
-  return 8.0 * (rd + wr) * nodes;
+  return 8.0 * (rd * inputs + wr * nodes);
 }
 
 // Run a segment program for a batch of nodes of one half.
@@ -182,7 +195,16 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
         L->nodes[j - j0].path = jobs[j].path;
       }
       void* e1 = nullptr;
-      if (prof) prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes), st, &e1);
+      if (prof) {
+        // siblings share their parent's buffer: count each input once (they
+        // read disjoint pinned parts when pins separate them, so count those
+        // as separate reads)
+        std::vector<std::pair<const void*, uint64_t>> ins;
+        for (int j = 0; j < L->n_nodes; j++) ins.push_back({L->nodes[j].in, pin_key(pp.dev, plan, L->nodes[j].path)});
+        std::sort(ins.begin(), ins.end());
+        const int uniq = (int)(std::unique(ins.begin(), ins.end()) - ins.begin());
+        prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes, uniq), st, &e1);
+      }
       if (pp.jit_id >= 0) launch_pass_jit(*L, tiles, plan.jit_entries[pp.jit_id], st);
       else launch_pass(*L, tiles, plan.fuse_bits, plan.tile_bits, st);
       if (prof) prof_end(plan, e1, st);
@@ -194,7 +216,7 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
 
 double segment_bytes(const SegmentPlan& s) {
   double b = 0;
-  for (auto& pp : s.passes) b += pass_bytes(pp.dev, 1);
+  for (auto& pp : s.passes) b += pass_bytes(pp.dev, 1, 1);
   return b;
 }
 

@@ -155,8 +155,11 @@ struct ItemGeo {
 __device__ __forceinline__ ItemGeo item_geo(const PassLaunch& P, int64_t item, int tiles_log2) {
   const DevPass& d = P.pass;
   ItemGeo g;
-  g.node = (int)(item >> tiles_log2);
-  const uint32_t t = (uint32_t)(item & ((1ll << tiles_log2) - 1));
+  // tile-major order: the launch's nodes take tile t one after another, so
+  // nodes that read one parent buffer (siblings) fetch each of its tiles from
+  // DRAM once and from L2 after that
+  g.node = (int)(item % P.n_nodes);
+  const uint32_t t = (uint32_t)(item / P.n_nodes);
   g.path = P.nodes[g.node].path;
   uint32_t base = 0;
   for (int i = 0; i < d.n_free; i++) base |= ((t >> i) & 1u) << d.freepos[i];
