@@ -201,7 +201,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
   std::ostringstream o;
   o << "namespace sf {\nstruct " << name << "_prog {\n"
     << "static __device__ __forceinline__ void run(const PassLaunch& P, float2* sm, const ItemGeo& g, "
-       "const float2* w8, int ncomp) {\n"
+       "const float2* w8, int ncomp, bool active) {\n"
     << "const uint32_t tid = threadIdx.x;\n(void)P; (void)g; (void)w8;\n";
   for (int s = 0; s < d.n_stages; s++) {
     const DevStage& st = pp.stages[s];
@@ -215,7 +215,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
       C[i] = c;
     }
     for (int j = 0; j < R; j++) gr[j] = d.gpos[st.rbit[j]];
-    o << "{ // stage " << s << "\n";
+    o << "if (active) { // stage " << s << "\n";
     o << "const uint32_t pf = swz(" << deposit(st.tpos, k - R) << ");\n";
     o << "const uint32_t gfix = g.base | " << deposit(st.tg, k - R) << ";\n(void)gfix;\n";
     o << "float2 v[" << NR << "];\n";
@@ -400,7 +400,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     } else {
       for (int i = 0; i < NR; i++) o << "*(" << at(i) << ") = v[" << i << "];\n";
     }
-    o << "compute_bar(ncomp);\n}\n";
+    o << "}\ncompute_bar(ncomp);\n";
   }
   o << "}\n";
   gen_copy(o, pp);

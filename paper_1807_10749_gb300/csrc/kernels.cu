@@ -120,99 +120,101 @@ __device__ __forceinline__ void apply_phase(const DevPhaseGroup& g, float2* v, u
 
 template <int R, bool GEN>
 __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
-                                           int ncomp) {
+                                           int ncomp, bool active) {
   const float post_scale = P.pass.post_scale;
   const DevPass& d = P.pass;
   const int k = d.k;
   for (int s = 0; s < d.n_stages; s++) {
-    const DevStage& st = P.stages[s];
-    uint32_t poff[R];
-    int gr[R];
+    if (active) {  // idle threads skip to the same barrier instruction
+      const DevStage& st = P.stages[s];
+      uint32_t poff[R];
+      int gr[R];
 #pragma unroll
-    for (int j = 0; j < R; j++) {
-      poff[j] = swz(1u << st.rbit[j]);
-      gr[j] = d.gpos[st.rbit[j]];
-    }
-    uint32_t lfix = 0, gfix = g.base;
-    for (int t = 0; t < k - R; t++) {
-      const uint32_t b = (threadIdx.x >> t) & 1u;
-      lfix |= b << st.tpos[t];
-      gfix |= b << st.tg[t];
-    }
-    const uint32_t pfix = swz(lfix);
-    float2 v[1 << R];
-    {
-      uint32_t addr = pfix;
-      v[0] = sm[addr];
-#pragma unroll
-      for (int i = 1; i < (1 << R); i++) {
-        const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
-        addr ^= poff[cctz(gi ^ prev)];
-        v[gi] = sm[addr];
+      for (int j = 0; j < R; j++) {
+        poff[j] = swz(1u << st.rbit[j]);
+        gr[j] = d.gpos[st.rbit[j]];
       }
-    }
-    for (int o = st.op_begin; o < st.op_end; o++) {
-      const DevOp& op = P.ops[o];
-      switch (op.code) {
-        case DOP_H:
-        case DOP_XH:
-        case DOP_YH:
-          dispatch_1q<R>(op.code, op.a, v);
-          break;
-        case DOP_PHASE:
-          apply_phase<R>(P.phases[op.arg], v, gfix, P.xshift, P.xbits, g.path, w8);
-          break;
-        default:
-          if constexpr (GEN) {
-            switch (op.code) {
-            case DOP_G1: {
-              const float* m = P.mats + 2 * op.arg;
-              dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
-                             make_float2(m[4], m[5]), make_float2(m[6], m[7]));
-              break;
-            }
-            case DOP_G1SEL: {
-              const int dg = digit_of(P.xshift, P.xbits, g.path, op.xi);
-              const float* m = P.mats + 2 * (op.arg + 4 * dg);
-              dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
-                             make_float2(m[4], m[5]), make_float2(m[6], m[7]));
-              break;
-            }
-            case DOP_G2:
-              dispatch_g2<R>(op.a, op.b, v, P.mats + 2 * op.arg);
-              break;
-            case DOP_DMUL: {
-              const float* m = P.mats + 2 * op.arg;
-              const float2 f0 = make_float2(m[0], m[1]), f1 = make_float2(m[2], m[3]);
-              int jr = -1;
+      uint32_t lfix = 0, gfix = g.base;
+      for (int t = 0; t < k - R; t++) {
+        const uint32_t b = (threadIdx.x >> t) & 1u;
+        lfix |= b << st.tpos[t];
+        gfix |= b << st.tg[t];
+      }
+      const uint32_t pfix = swz(lfix);
+      float2 v[1 << R];
+      {
+        uint32_t addr = pfix;
+        v[0] = sm[addr];
 #pragma unroll
-              for (int j = 0; j < R; j++)
-                if (gr[j] == op.a) jr = j;
-              if (jr >= 0) {
-                dispatch_dmul<R>(jr, v, f0, f1);
-              } else {
-                const float2 f = ((gfix >> op.a) & 1u) ? f1 : f0;
-#pragma unroll
-                for (int i = 0; i < (1 << R); i++) v[i] = cmul(f, v[i]);
-              }
-              break;
-            }
-            default:
+        for (int i = 1; i < (1 << R); i++) {
+          const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
+          addr ^= poff[cctz(gi ^ prev)];
+          v[gi] = sm[addr];
+        }
+      }
+      for (int o = st.op_begin; o < st.op_end; o++) {
+        const DevOp& op = P.ops[o];
+        switch (op.code) {
+          case DOP_H:
+          case DOP_XH:
+          case DOP_YH:
+            dispatch_1q<R>(op.code, op.a, v);
+            break;
+          case DOP_PHASE:
+            apply_phase<R>(P.phases[op.arg], v, gfix, P.xshift, P.xbits, g.path, w8);
+            break;
+          default:
+            if constexpr (GEN) {
+              switch (op.code) {
+              case DOP_G1: {
+                const float* m = P.mats + 2 * op.arg;
+                dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                               make_float2(m[4], m[5]), make_float2(m[6], m[7]));
                 break;
-            }
-          }
-          break;
-      }
-    }
-    const float sc = (s == d.n_stages - 1) ? post_scale : 1.0f;
-    {
-      uint32_t addr = pfix;
-      sm[addr] = make_float2(v[0].x * sc, v[0].y * sc);
+              }
+              case DOP_G1SEL: {
+                const int dg = digit_of(P.xshift, P.xbits, g.path, op.xi);
+                const float* m = P.mats + 2 * (op.arg + 4 * dg);
+                dispatch_g1<R>(op.a, v, make_float2(m[0], m[1]), make_float2(m[2], m[3]),
+                               make_float2(m[4], m[5]), make_float2(m[6], m[7]));
+                break;
+              }
+              case DOP_G2:
+                dispatch_g2<R>(op.a, op.b, v, P.mats + 2 * op.arg);
+                break;
+              case DOP_DMUL: {
+                const float* m = P.mats + 2 * op.arg;
+                const float2 f0 = make_float2(m[0], m[1]), f1 = make_float2(m[2], m[3]);
+                int jr = -1;
 #pragma unroll
-      for (int i = 1; i < (1 << R); i++) {
-        const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
-        addr ^= poff[cctz(gi ^ prev)];
-        sm[addr] = make_float2(v[gi].x * sc, v[gi].y * sc);
+                for (int j = 0; j < R; j++)
+                  if (gr[j] == op.a) jr = j;
+                if (jr >= 0) {
+                  dispatch_dmul<R>(jr, v, f0, f1);
+                } else {
+                  const float2 f = ((gfix >> op.a) & 1u) ? f1 : f0;
+#pragma unroll
+                  for (int i = 0; i < (1 << R); i++) v[i] = cmul(f, v[i]);
+                }
+                break;
+              }
+              default:
+                  break;
+              }
+            }
+            break;
+        }
+      }
+      const float sc = (s == d.n_stages - 1) ? post_scale : 1.0f;
+      {
+        uint32_t addr = pfix;
+        sm[addr] = make_float2(v[0].x * sc, v[0].y * sc);
+#pragma unroll
+        for (int i = 1; i < (1 << R); i++) {
+          const int gi = i ^ (i >> 1), prev = (i - 1) ^ ((i - 1) >> 1);
+          addr ^= poff[cctz(gi ^ prev)];
+          sm[addr] = make_float2(v[gi].x * sc, v[gi].y * sc);
+        }
       }
     }
     compute_bar(ncomp);
@@ -224,8 +226,8 @@ __device__ __forceinline__ void run_stages(const PassLaunch& P, float2* sm, cons
 template <int R, bool GEN>
 struct GenericProg : GenericCopy {
   static __device__ __forceinline__ void run(const PassLaunch& P, float2* sm, const ItemGeo& g, const float2* w8,
-                                             int ncomp) {
-    run_stages<R, GEN>(P, sm, g, w8, ncomp);
+                                             int ncomp, bool active) {
+    run_stages<R, GEN>(P, sm, g, w8, ncomp, active);
   }
 };
 

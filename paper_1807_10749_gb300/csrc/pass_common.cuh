@@ -281,8 +281,9 @@ struct GenericCopy {
   }
 };
 
-// Prog::run(P, sm, g, w8, ncomp) runs the register stages of one tile (the
-// threads below 2^(k-R)); the other compute threads only join its barriers.
+// Prog::run(P, sm, g, w8, ncomp, active) runs the register stages of one
+// tile: every compute thread calls it and passes each stage barrier at the
+// same instruction; only active threads (below 2^(k-R)) do stage work.
 // Prog::load_tile / Prog::store_tile move a tile between its node buffer and
 // shared memory (load warp: cp.async into dst; store warp: vector stores).
 template <int R, class Prog>
@@ -403,9 +404,9 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         if (((uint32_t)e & g.lin_m) != g.lin_v) sm[swz(e)] = make_float2(0.f, 0.f);
       compute_bar(ncomp);
     }
-    if (threadIdx.x < nact) Prog::run(P, sm, g, w8, ncomp);
-    else
-      for (int s = 0; s < d.n_stages; s++) compute_bar(ncomp);
+    // every compute thread runs the stage program, so that all of them pass
+    // the same barrier instructions; threads above 2^(k-R) skip the work
+    Prog::run(P, sm, g, w8, ncomp, (int)threadIdx.x < nact);
     if (d.n_stages == 0 && d.post_scale != 1.0f) {
       for (int e = threadIdx.x; e < ntile; e += ncomp) {
         float2 v = sm[e];
