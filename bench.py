@@ -429,7 +429,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
                                               "tile_bits": args.tile_bits or 12, "fuse_bits": args.fuse_bits or 5,
-                                              "run_bits": args.run_bits or 4,
+                                              "run_bits": args.run_bits or "per segment (3 or 4)",
                                               "pass_kernels": "specialised" if args.jit else "generic",
                                               "split_last": args.split_last,
                                               "plan_seconds": t_plan,

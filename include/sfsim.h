@@ -105,7 +105,9 @@ typedef struct {
                                 free memory at plan time */
   int32_t batch_paths;       /* max leaf groups per launch, 0 = from budget */
   int32_t run_bits;          /* log2 contiguous amplitudes per copy run (the
-                                index bits every pass keeps active), 0 = 4 */
+                                index bits every pass keeps active), 0 = per
+                                segment the width (4 or 3) whose program moves
+                                fewer bytes */
   int32_t jit;              /* 1 = compile every pass of the plan into a kernel of
                                its own at plan time (NVRTC; SF_EUNSUPPORTED where
                                NVRTC is missing), 0 = the generic pass kernel */

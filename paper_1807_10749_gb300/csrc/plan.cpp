@@ -751,6 +751,29 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
 }  // namespace
 
 // ------------------------------------------------------------ plan create
+// Plan a segment with the given run width, or, when the width is automatic
+// (run_bits option 0), with widths 3 and 4 and keep the program with fewer
+// algorithmic bytes (the wider runs on a tie: longer contiguous copies).
+void plan_segment_auto(int m, const std::vector<HOp>& ops, const std::vector<Pin>& pins, bool first, const Plan& P,
+                       bool auto_runs, SegmentPlan& out) {
+  if (!auto_runs) {
+    plan_segment(m, ops, pins, first, P.tile_bits, P.fuse_bits, P.run_bits, out);
+    return;
+  }
+  SegmentPlan best;
+  double best_b = -1;
+  for (int rb : {4, 3}) {
+    SegmentPlan cand;
+    plan_segment(m, ops, pins, first, P.tile_bits, P.fuse_bits, rb, cand);
+    const double b = segment_bytes(cand);
+    if (best_b < 0 || b < best_b) {
+      best = std::move(cand);
+      best_b = b;
+    }
+  }
+  out = std::move(best);
+}
+
 Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
   Plan* P = new Plan();
   try {
@@ -1000,19 +1023,19 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
       }
     }
     // pass programs
+    const bool auto_runs = o.run_bits == 0;
     for (int side = 0; side < 2; side++) {
       HalfPlan& H = side ? P->B : P->A;
       H.seg.assign(nL + 1, SegmentPlan());
       std::vector<Pin> pins = H.root_pins;
       for (int s = 0; s <= nL; s++) {
-        plan_segment(H.m, H.seg_ops[s], pins, s == 0, P->tile_bits, P->fuse_bits, P->run_bits, H.seg[s]);
+        plan_segment_auto(H.m, H.seg_ops[s], pins, s == 0, *P, auto_runs, H.seg[s]);
         H.seg[s].scale *= seg_global[2 * s + side];
         pins = H.seg[s].pins_out;
       }
       if (P->deferred) {
         std::vector<Pin> pin_in = nL >= 1 ? H.seg[nL - 1].pins_out : H.root_pins;
-        plan_segment(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, P->tile_bits, P->fuse_bits, P->run_bits,
-                     H.last_deferred);
+        plan_segment_auto(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, *P, auto_runs, H.last_deferred);
         H.last_deferred.scale *= seg_global[2 * nL + side];
         if (!o.split_last) {
           // no branching happens at the folded level, so the segment that
@@ -1020,7 +1043,7 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
           std::vector<HOp> ops = H.seg_ops[nL - 1];
           ops.insert(ops.end(), H.seg_ops[nL + 1].begin(), H.seg_ops[nL + 1].end());
           std::vector<Pin> pin_m = nL >= 2 ? H.seg[nL - 2].pins_out : H.root_pins;
-          plan_segment(H.m, ops, pin_m, nL == 1, P->tile_bits, P->fuse_bits, P->run_bits, H.last_merged);
+          plan_segment_auto(H.m, ops, pin_m, nL == 1, *P, auto_runs, H.last_merged);
           H.last_merged.scale *= seg_global[2 * (nL - 1) + side] * seg_global[2 * nL + side];
         }
       }
