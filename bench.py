@@ -428,7 +428,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
-                                              "tile_bits": args.tile_bits or 12, "fuse_bits": args.fuse_bits or 5,
+                                              "tile_bits": args.tile_bits or "per segment (12 or 13)", "fuse_bits": args.fuse_bits or 5,
                                               "run_bits": args.run_bits or "per segment (3 or 4)",
                                               "pass_kernels": "specialised" if args.jit else "generic",
                                               "split_last": args.split_last,

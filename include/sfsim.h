@@ -95,7 +95,8 @@ typedef struct {
                                 block, then the number of cross gates) */
   int32_t decomposition;     /* SF_DEC_* for non-CZ cross gates */
   int32_t select_prefix_bits;/* x_s of FRACTION selection; -1 = max(0, x-7) */
-  int32_t tile_bits;         /* log2 amplitudes per tile (<= 13), 0 = 12 */
+  int32_t tile_bits;         /* log2 amplitudes per tile (<= 13), 0 = per segment
+                                12 or 13, whichever is estimated faster */
   int32_t fuse_bits;         /* log2 amplitudes per thread register block
                                 (fusion width), 0 = tuned default */
   int32_t exec_mode;         /* SF_EXEC_* */

@@ -751,26 +751,30 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
 }  // namespace
 
 // ------------------------------------------------------------ plan create
-// Plan a segment with the given run width, or, when the width is automatic
-// (run_bits option 0), with widths 3 and 4 and keep the program with fewer
-// algorithmic bytes (the wider runs on a tie: longer contiguous copies).
+// Plan a segment. With an automatic tile size (tile_bits option 0) the
+// candidates are 2^12 and 2^13 amplitudes, with an automatic run width
+// (run_bits option 0) widths 4 and 3; the program with the least estimated
+// time wins: algorithmic bytes divided by the fraction of HBM bandwidth the
+// pass kernel reaches at that tile size on GB300 (2^12: two CTAs per SM,
+// ~0.75; 2^13: one CTA per SM, ~0.64; measured on the 7x8 workload). Ties go
+// to the wider runs (longer contiguous copies).
 void plan_segment_auto(int m, const std::vector<HOp>& ops, const std::vector<Pin>& pins, bool first, const Plan& P,
-                       bool auto_runs, SegmentPlan& out) {
-  if (!auto_runs) {
-    plan_segment(m, ops, pins, first, P.tile_bits, P.fuse_bits, P.run_bits, out);
-    return;
-  }
+                       bool auto_tiles, bool auto_runs, SegmentPlan& out) {
+  std::vector<int> tiles = auto_tiles ? std::vector<int>{12, 13} : std::vector<int>{P.tile_bits};
+  std::vector<int> runs = auto_runs ? std::vector<int>{4, 3} : std::vector<int>{P.run_bits};
   SegmentPlan best;
-  double best_b = -1;
-  for (int rb : {4, 3}) {
-    SegmentPlan cand;
-    plan_segment(m, ops, pins, first, P.tile_bits, P.fuse_bits, rb, cand);
-    const double b = segment_bytes(cand);
-    if (best_b < 0 || b < best_b) {
-      best = std::move(cand);
-      best_b = b;
+  double best_t = -1;
+  for (int tb : tiles)
+    for (int rb : runs) {
+      SegmentPlan cand;
+      plan_segment(m, ops, pins, first, tb, P.fuse_bits, rb, cand);
+      const double eff = std::min(tb, m) >= 13 ? 0.64 : 0.75;
+      const double t = segment_bytes(cand) / eff;
+      if (best_t < 0 || t < best_t * (1 - 1e-9)) {
+        best = std::move(cand);
+        best_t = t;
+      }
     }
-  }
   out = std::move(best);
 }
 
@@ -790,8 +794,9 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
     if (mA > 32 || mB > 32) fail(SF_EUNSUPPORTED, "a half of more than 32 qubits");
     if (mA < 1 || mB < 1) fail(SF_EINVAL, "empty half");
     // the pipelined pass kernel holds three tile buffers of 2^k complex64 in
-    // shared memory, so k <= 13; the default k = 12 (96 KiB per CTA) lets two
-    // CTAs, i.e. two independent copy/compute pipelines, share an SM
+    // shared memory, so k <= 13; with tile_bits 0 each segment takes k = 12
+    // (96 KiB per CTA: two CTAs, i.e. two copy/compute pipelines, per SM) or
+    // k = 13 (one CTA per SM, fewer passes), whichever is estimated faster
     P->tile_bits = o.tile_bits > 0 ? std::min(o.tile_bits, 13) : 12;
     P->fuse_bits = o.fuse_bits > 0 ? std::min(o.fuse_bits, MAX_R) : 5;
     P->run_bits = o.run_bits > 0 ? std::min(o.run_bits, 8) : 4;
@@ -1023,19 +1028,19 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
       }
     }
     // pass programs
-    const bool auto_runs = o.run_bits == 0;
+    const bool auto_runs = o.run_bits == 0, auto_tiles = o.tile_bits == 0;
     for (int side = 0; side < 2; side++) {
       HalfPlan& H = side ? P->B : P->A;
       H.seg.assign(nL + 1, SegmentPlan());
       std::vector<Pin> pins = H.root_pins;
       for (int s = 0; s <= nL; s++) {
-        plan_segment_auto(H.m, H.seg_ops[s], pins, s == 0, *P, auto_runs, H.seg[s]);
+        plan_segment_auto(H.m, H.seg_ops[s], pins, s == 0, *P, auto_tiles, auto_runs, H.seg[s]);
         H.seg[s].scale *= seg_global[2 * s + side];
         pins = H.seg[s].pins_out;
       }
       if (P->deferred) {
         std::vector<Pin> pin_in = nL >= 1 ? H.seg[nL - 1].pins_out : H.root_pins;
-        plan_segment_auto(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, *P, auto_runs, H.last_deferred);
+        plan_segment_auto(H.m, H.seg_ops[nL + 1], pin_in, nL == 0, *P, auto_tiles, auto_runs, H.last_deferred);
         H.last_deferred.scale *= seg_global[2 * nL + side];
         if (!o.split_last) {
           // no branching happens at the folded level, so the segment that
@@ -1043,7 +1048,7 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
           std::vector<HOp> ops = H.seg_ops[nL - 1];
           ops.insert(ops.end(), H.seg_ops[nL + 1].begin(), H.seg_ops[nL + 1].end());
           std::vector<Pin> pin_m = nL >= 2 ? H.seg[nL - 2].pins_out : H.root_pins;
-          plan_segment_auto(H.m, ops, pin_m, nL == 1, *P, auto_runs, H.last_merged);
+          plan_segment_auto(H.m, ops, pin_m, nL == 1, *P, auto_tiles, auto_runs, H.last_merged);
           H.last_merged.scale *= seg_global[2 * (nL - 1) + side] * seg_global[2 * nL + side];
         }
       }
