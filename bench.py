@@ -165,7 +165,7 @@ def max_over_ranks(value, device=None):
     return float(t.item())
 
 
-def serving_window(sfsim, inputs, n_req=24, seed=42, max_paths=1 << 17, load=0.8):
+def serving_window(sfsim, inputs, n_req=24, seed=42, max_paths=1 << 17, load=0.8, jit=1):
     """Serving mix (time-boxed): requests drawn like the 2000-request stream -
     grids uniform over 4x5, 5x5, 5x6, 6x6, 6x7, depth 1+d+1 with d uniform in
     16..32, f log-uniform in [0.01, 1], 1e3..1e6 bitstrings log-uniform -
@@ -183,12 +183,14 @@ def serving_window(sfsim, inputs, n_req=24, seed=42, max_paths=1 << 17, load=0.8
         d = int(rng.integers(16, 33))
         f = float(np.exp(rng.uniform(np.log(0.01), 0.0)))
         na = int(np.exp(rng.uniform(np.log(1e3), np.log(1e6))))
-        plan = sfsim.Plan(inputs.google_circuit(R, C, d, 1 + len(reqs)).text())
+        text = inputs.google_circuit(R, C, d, 1 + len(reqs)).text()
+        plan = sfsim.Plan(text)
         sel = sfsim.selection("fraction", fidelity=f, seed=7 + len(reqs))
         npaths, _ = sfsim.sf_selection_size(plan.handle, sel)
+        plan.close()
         if npaths > max_paths:
-            plan.close()
             continue
+        plan = sfsim.Plan(text, jit=jit)   # kernels compiled here, before any timing
         bits = inputs.random_bitstrings(R * C, na, 2000 + len(reqs))
         reqs.append((plan, bits, sel, npaths))
     alone, t_alone = [], []
@@ -235,7 +237,8 @@ def serving_window(sfsim, inputs, n_req=24, seed=42, max_paths=1 << 17, load=0.8
                   "plain_paths_per_s": paths / t_seq, "served_paths_per_s": paths / makespan,
                   "served_identical_to_alone": same, "makespan_s": makespan, "plain_total_s": t_seq,
             "saturated_paths_per_s": paths / saturated,
-            "window": f"first {n_req} requests of the seeded mix with <= {max_paths} paths"}
+            "window": f"first {n_req} requests of the seeded mix with <= {max_paths} paths",
+            "pass_kernels": "specialised" if jit else "generic"}
 
 
 def run_reference(args):
@@ -413,7 +416,7 @@ def main():
         pplan.close()
     serving = None
     if world == 1 and not args.no_serve and args.workload == WORKLOAD:
-        serving = serving_window(sfsim, inputs)
+        serving = serving_window(sfsim, inputs, jit=args.jit)
 
     if rank == 0:
         peak, peak_kind = measured_peaks()
