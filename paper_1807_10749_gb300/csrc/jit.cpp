@@ -122,7 +122,10 @@ std::string deposit(const int8_t* pos, int nbits) {
 void gen_copy(std::ostringstream& o, const PassPlan& pp) {
   const DevPass& d = pp.dev;
   if (d.k < 6) {  // fewer chunks than lanes: the generic loops
-    o << "};\nstruct sf_pass_spec_copy : GenericCopy {\n";
+    o << "static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, "
+         "int lane, const CopyCtx& cc) { GenericCopy::load_tile(P, g, dst, lane, cc); }\n"
+      << "static __device__ __forceinline__ void store_tile(const PassLaunch& P, const ItemGeo& g, "
+         "const float2* buf, int lane, const CopyCtx& cc) { GenericCopy::store_tile(P, g, buf, lane, cc); }\n";
     return;
   }
   const int k = d.k, L = d.L, nj = 1 << (k - 6);
@@ -154,43 +157,40 @@ void gen_copy(std::ostringstream& o, const PassPlan& pp) {
   }
   std::string gl = deposit(lpos, 5);
   for (size_t at; (at = gl.find("tid")) != std::string::npos;) gl.replace(at, 3, "ln");
-  // Per-j constants in a table (one warp-uniform constant load per chunk),
-  // so the copy loops stay short: the copy warps share the instruction
-  // cache with the stage program.
-  //   x: global element offset G_j;  y: bits 0..3 lo_j, bits 4..31 the run
-  //   bits of j (e >> L) for the pin test
-  o << "};\n__constant__ uint2 " << "sfc_tab[" << nj << "] = {";
-  for (int j = 0; j < nj; j++) o << (j ? "," : "") << "{" << G[j] << "u," << (lo[j] | (rj[j] << 4)) << "u}";
-  o << "};\nstruct sf_pass_spec_copy {\n";
   // loads
   o << "static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, "
        "int lane, const CopyCtx&) {\n"
     << "const uint32_t ln = (uint32_t)lane;\n"
     << "const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in) + (g.base | " << gl << ");\n"
     << "const uint32_t s2 = swz(2u * ln);\n";
+  for (int q = 0; q < nlow; q++) o << "const uint32_t d" << q << " = dst + 8u * (s2 ^ " << lows[q] << "u);\n";
   if (rm_in) o << "const uint32_t rl = ((2u * ln) >> " << L << ") & " << rm_in << "u, rv = g.lin_v >> " << L << ";\n";
-  o << "#pragma unroll 4\nfor (int j = 0; j < " << nj << "; j++) {\n"
-    << "const uint2 t = sfc_tab[j];\n";
-  if (rm_in) o << "if ((rl | ((t.y >> 4) & " << rm_in << "u)) != rv) continue;\n";
-  o << "cp_async16(dst + 8u * (s2 ^ (t.y & 0xFu)) + 512u * (uint32_t)j, in + t.x);\n}\n}\n";
-  // stores, four chunks in flight per lane
+  for (int j = 0; j < nj; j++) {
+    if (rm_in) o << "if ((rl | " << (rj[j] & rm_in) << "u) == rv) ";
+    o << "cp_async16(d" << lid[j] << " + " << 512u * j << "u, in + " << G[j] << "u);\n";
+  }
+  o << "}\n";
+  // stores, eight chunks in flight per lane
   o << "static __device__ __forceinline__ void store_tile(const PassLaunch& P, const ItemGeo& g, const float2* buf, "
        "int lane, const CopyCtx&) {\n"
     << "const uint32_t ln = (uint32_t)lane;\n"
     << "float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out) + (g.base | " << gl << ");\n"
-    << "const uint32_t s2 = swz(2u * ln);\n"
-    << "const float4* b4 = reinterpret_cast<const float4*>(buf);\n";
+    << "const uint32_t s2 = swz(2u * ln);\n";
+  for (int q = 0; q < nlow; q++)
+    o << "const float4* b" << q << " = reinterpret_cast<const float4*>(buf + (s2 ^ " << lows[q] << "u));\n";
   if (rm_out)
     o << "const uint32_t rl = ((2u * ln) >> " << L << ") & " << rm_out << "u, rv = g.lout_v >> " << L << ";\n";
-  const int u = std::min(nj, 4);
-  o << "for (int j0 = 0; j0 < " << nj << "; j0 += " << u << ") {\n"
-    << "float4 q[" << u << "];\nuint2 t[" << u << "];\n"
-    << "#pragma unroll\nfor (int i = 0; i < " << u << "; i++) {\n"
-    << "t[i] = sfc_tab[j0 + i];\n"
-    << "q[i] = b4[((s2 ^ (t[i].y & 0xFu)) >> 1) + 32u * (uint32_t)(j0 + i)];\n}\n"
-    << "#pragma unroll\nfor (int i = 0; i < " << u << "; i++) {\n";
-  if (rm_out) o << "if ((rl | ((t[i].y >> 4) & " << rm_out << "u)) != rv) continue;\n";
-  o << "*reinterpret_cast<float4*>(out + t[i].x) = q[i];\n}\n}\n}\n";
+  for (int j0 = 0; j0 < nj; j0 += 8) {
+    o << "{\n";
+    for (int j = j0; j < std::min(nj, j0 + 8); j++)
+      o << "const float4 q" << j - j0 << " = b" << lid[j] << "[" << 32u * j << "u];\n";
+    for (int j = j0; j < std::min(nj, j0 + 8); j++) {
+      if (rm_out) o << "if ((rl | " << (rj[j] & rm_out) << "u) == rv) ";
+      o << "*reinterpret_cast<float4*>(out + " << G[j] << "u) = q" << j - j0 << ";\n";
+    }
+    o << "}\n";
+  }
+  o << "}\n";
 }
 
 // One pass as a stage program: struct `name`_prog in namespace sf and an
@@ -199,7 +199,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
   const DevPass& d = pp.dev;
   const int R = d.R, k = d.k, NR = 1 << R;
   std::ostringstream o;
-  o << "namespace sf {\nstruct " << name << "_stages {\n"
+  o << "namespace sf {\nstruct " << name << "_prog {\n"
     << "static __device__ __forceinline__ void run(const PassLaunch& P, float2* sm, const ItemGeo& g, "
        "const float2* w8, int ncomp, bool active) {\n"
     << "const uint32_t tid = threadIdx.x;\n(void)P; (void)g; (void)w8;\n";
@@ -404,7 +404,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
   }
   o << "}\n";
   gen_copy(o, pp);
-  o << "};\nstruct " << name << "_prog : " << name << "_stages, sf_pass_spec_copy {};\n}  // namespace sf\n";
+  o << "};\n}  // namespace sf\n";
   const int threads = (((1 << (k - R)) + 31) / 32) * 32 + 64;  // stage warps + the two copy warps
   // tiles of up to 2^12 amplitudes leave shared memory for two CTAs per SM:
   // ask for the registers to allow it as well
