@@ -246,6 +246,18 @@ def sf_amplitudes(plan, bitstrings, sel):
     return out[0::2] + 1j * out[1::2], fa.value
 
 
+def sf_amplitudes_into(plan, bits_u64, sel, out_f64):
+    """Host form into caller buffers (e.g. pinned): bits_u64 a contiguous
+    uint64 array, out_f64 a contiguous float64 array of 2n (re, im). Returns
+    f_actual."""
+    assert bits_u64.dtype == np.uint64 and bits_u64.flags["C_CONTIGUOUS"]
+    assert out_f64.dtype == np.float64 and out_f64.flags["C_CONTIGUOUS"] and out_f64.size >= 2 * bits_u64.size
+    fa = ctypes.c_double()
+    _check(lib().sf_amplitudes(plan, _ptr(bits_u64), bits_u64.size, ctypes.byref(sel), _ptr(out_f64),
+                               ctypes.byref(fa)))
+    return fa.value
+
+
 def sf_workspace_size(plan, n, sel) -> int:
     b = ctypes.c_size_t()
     _check(lib().sf_workspace_size(plan, n, ctypes.byref(sel), ctypes.byref(b)))

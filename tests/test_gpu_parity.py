@@ -167,6 +167,12 @@ def test_device_form_matches_host_form():
     o = d_out.cpu().numpy()
     dev = o[:, 0] + 1j * o[:, 1]
     assert np.abs(dev - 2 * host).max() <= 1e-12 * 2.0 ** -8
+    # host form into caller-owned pinned buffers
+    pin_bits = torch.from_numpy(bits.view(np.int64)).pin_memory().numpy().view(np.uint64)
+    pin_out = torch.empty(2 * len(bits), dtype=torch.float64).pin_memory().numpy()
+    fa = sfsim.sf_amplitudes_into(p.handle, pin_bits, sel, pin_out)
+    assert fa == 1.0
+    assert np.array_equal(pin_out[0::2] + 1j * pin_out[1::2], host)
     p.close()
 
 
