@@ -296,6 +296,8 @@ def main():
     ap.add_argument("--run-bits", type=int, default=0)
     ap.add_argument("--split-last", type=int, default=0, choices=[0, 1],
                     help="1: run the level before the folded last level as its own segment")
+    ap.add_argument("--fp32x2", type=int, default=1, choices=[0, 1],
+                    help="1: packed FP32x2 arithmetic in the specialised kernels' Google-gate stages")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1],
                     help="1: per-pass specialised kernels compiled at plan time; 0: the generic pass kernel")
     args = ap.parse_args()
@@ -329,7 +331,7 @@ def main():
     t_plan = time.perf_counter()
     plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode, tile_bits=args.tile_bits,
                       fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit,
-                      split_last=args.split_last)
+                      split_last=args.split_last, fp32x2=args.fp32x2)
     t_plan = time.perf_counter() - t_plan
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
@@ -435,7 +437,7 @@ def main():
                                               "tile_bits": args.tile_bits or "per segment (12 or 13)", "fuse_bits": args.fuse_bits or 5,
                                               "run_bits": args.run_bits or "per segment (3 or 4)",
                                               "pass_kernels": "specialised" if args.jit else "generic",
-                                              "split_last": args.split_last,
+                                              "split_last": args.split_last, "fp32x2": args.fp32x2,
                                               "plan_seconds": t_plan,
                                               "paths_selected": n_sel, "parallelism": f"paths x{world}",
                                               "wall_s": wall}),

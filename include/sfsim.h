@@ -116,7 +116,11 @@ typedef struct {
                                the level before it and the last segment as one
                                program (no node is written between them), 1 = two
                                programs with the node in between */
-  int32_t reserved[4];
+  int32_t fp32x2;           /* specialised kernels: 1 = register stages made only of
+                               H, X^1/2, Y^1/2 and phase groups hold amplitude
+                               pairs in FP32x2 registers (packed adds), 0 = scalar.
+                               sf_plan_opts_default sets 1 */
+  int32_t reserved[3];
 } sf_plan_opts;
 
 SF_API void sf_plan_opts_default(sf_plan_opts* o);

@@ -195,7 +195,7 @@ void gen_copy(std::ostringstream& o, const PassPlan& pp) {
 
 // One pass as a stage program: struct `name`_prog in namespace sf and an
 // extern "C" kernel `name`.
-std::string gen_pass(const PassPlan& pp, const std::string& name) {
+std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
   const DevPass& d = pp.dev;
   const int R = d.R, k = d.k, NR = 1 << R;
   std::ostringstream o;
@@ -215,10 +215,36 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
       C[i] = c;
     }
     for (int j = 0; j < R; j++) gr[j] = d.gpos[st.rbit[j]];
-    o << "if (active) { // stage " << s << "\n";
+    // Packed form (FP32x2): stages of H, X^1/2, Y^1/2 and phase groups only.
+    // Register bit p (the one with the fewest non-diagonal gates) pairs the
+    // amplitudes: Vr[s] = (re of lane 0, re of lane 1), Vi[s] likewise, so a
+    // butterfly on any other register bit is 4 FP32x2 adds per 4 amplitudes.
+    bool packed = pack && R >= 2;
+    int cnt[MAX_R] = {0};
+    for (int oi = st.op_begin; oi < st.op_end && packed; oi++) {
+      const DevOp& op = pp.ops[oi];
+      if (op.code == DOP_H || op.code == DOP_XH || op.code == DOP_YH) cnt[op.a]++;
+      else if (op.code != DOP_PHASE) packed = false;
+    }
+    int p = 0;
+    for (int j = 1; j < R; j++)
+      if (cnt[j] < cnt[p]) p = j;
+    auto slot = [&](int i) { return (i & ((1 << p) - 1)) | ((i >> (p + 1)) << p); };
+    auto RE = [&](int i) {
+      return packed ? "Vr[" + std::to_string(slot(i)) + "]." + (((i >> p) & 1) ? "y" : "x")
+                    : "v[" + std::to_string(i) + "].x";
+    };
+    auto IM = [&](int i) {
+      return packed ? "Vi[" + std::to_string(slot(i)) + "]." + (((i >> p) & 1) ? "y" : "x")
+                    : "v[" + std::to_string(i) + "].y";
+    };
+    o << "if (active) { // stage " << s << (packed ? " (packed)" : "") << "\n";
     o << "const uint32_t pf = swz(" << deposit(st.tpos, k - R) << ");\n";
     o << "const uint32_t gfix = g.base | " << deposit(st.tg, k - R) << ";\n(void)gfix;\n";
-    o << "float2 v[" << NR << "];\n";
+    if (packed)
+      o << "float2 Vr[" << NR / 2 << "], Vi[" << NR / 2 << "];\nconst float2 M1 = make_float2(-1.f, -1.f);\n(void)M1;\n";
+    else
+      o << "float2 v[" << NR << "];\n";
     // Addresses pf ^ C_i: the swizzle only touches bits 1..3, so with
     // pf = ph | pl and C_i = h_i | l_i split at bit 4, pf ^ C_i =
     // (ph | (pl ^ l_i)) + h_i. One base pointer per distinct low part l, and a
@@ -244,9 +270,13 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     if (j0 >= 0) {
       for (int i = 0; i < NR; i++) {
         if ((i >> j0) & 1) continue;
-        o << "{ const float4 q = *reinterpret_cast<const float4*>(" << at(i) << "); v[" << i
-          << "] = make_float2(q.x, q.y); v[" << (i | (1 << j0)) << "] = make_float2(q.z, q.w); }\n";
+        const int i1 = i | (1 << j0);
+        o << "{ const float4 q = *reinterpret_cast<const float4*>(" << at(i) << "); " << RE(i) << " = q.x; "
+          << IM(i) << " = q.y; " << RE(i1) << " = q.z; " << IM(i1) << " = q.w; }\n";
       }
+    } else if (packed) {
+      for (int i = 0; i < NR; i++)
+        o << "{ const float2 t = *(" << at(i) << "); " << RE(i) << " = t.x; " << IM(i) << " = t.y; }\n";
     } else {
       for (int i = 0; i < NR; i++) o << "v[" << i << "] = *(" << at(i) << ");\n";
     }
@@ -254,6 +284,43 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     o << "int kst = 0;\n";
     for (int oi = st.op_begin; oi < st.op_end; oi++) {
       const DevOp& op = pp.ops[oi];
+      if (packed && (op.code == DOP_H || op.code == DOP_XH || op.code == DOP_YH)) {
+        if (op.a == p) {  // within the pairs: scalar on the components
+          for (int i0 = 0; i0 < NR; i0++) {
+            if ((i0 >> p) & 1) continue;
+            const int i1 = i0 | (1 << p);
+            o << "{ const float ar = " << RE(i0) << ", ai = " << IM(i0) << ", br = " << RE(i1) << ", bi = " << IM(i1)
+              << "; ";
+            if (op.code == DOP_H)
+              o << RE(i0) << " = ar + br; " << IM(i0) << " = ai + bi; " << RE(i1) << " = ar - br; " << IM(i1)
+                << " = ai - bi; }\n";
+            else if (op.code == DOP_XH)
+              o << RE(i0) << " = ar + bi; " << IM(i0) << " = ai - br; " << RE(i1) << " = br + ai; " << IM(i1)
+                << " = bi - ar; }\n";
+            else
+              o << RE(i0) << " = ar - br; " << IM(i0) << " = ai - bi; " << RE(i1) << " = ar + br; " << IM(i1)
+                << " = ai + bi; }\n";
+          }
+        } else {  // across slots: FP32x2 butterflies (b * -1 + a is exact a - b)
+          const int jb = op.a < p ? op.a : op.a - 1;
+          for (int s0 = 0; s0 < NR / 2; s0++) {
+            if ((s0 >> jb) & 1) continue;
+            const std::string S0 = std::to_string(s0), S1 = std::to_string(s0 | (1 << jb));
+            o << "{ const float2 ar = Vr[" << S0 << "], ai = Vi[" << S0 << "], br = Vr[" << S1 << "], bi = Vi[" << S1
+              << "]; ";
+            if (op.code == DOP_H)
+              o << "Vr[" << S0 << "] = __fadd2_rn(ar, br); Vi[" << S0 << "] = __fadd2_rn(ai, bi); Vr[" << S1
+                << "] = __ffma2_rn(br, M1, ar); Vi[" << S1 << "] = __ffma2_rn(bi, M1, ai); }\n";
+            else if (op.code == DOP_XH)
+              o << "Vr[" << S0 << "] = __fadd2_rn(ar, bi); Vi[" << S0 << "] = __ffma2_rn(br, M1, ai); Vr[" << S1
+                << "] = __fadd2_rn(br, ai); Vi[" << S1 << "] = __ffma2_rn(ar, M1, bi); }\n";
+            else
+              o << "Vr[" << S0 << "] = __ffma2_rn(br, M1, ar); Vi[" << S0 << "] = __ffma2_rn(bi, M1, ai); Vr[" << S1
+                << "] = __fadd2_rn(ar, br); Vi[" << S1 << "] = __fadd2_rn(ai, bi); }\n";
+          }
+        }
+        continue;
+      }
       switch (op.code) {
         case DOP_H:
           o << "g_h<" << R << ", " << op.a << ">(v);\n";
@@ -310,7 +377,9 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
                   if (((i >> l) & 1) && ((G.czq[j] >> l) & 1)) ku += 4;
               }
             ku &= 7;
-            if (ku) o << "v[" << i << "] = omega_mul<" << ku << ">(v[" << i << "]);\n";
+            if (ku)
+              o << "{ const float2 a = omega_mul<" << ku << ">(make_float2(" << RE(i) << ", " << IM(i) << ")); "
+                << RE(i) << " = a.x; " << IM(i) << " = a.y; }\n";
           }
           // per-thread scalar part (fixed index bits), summed over the stage
           auto kadd = [&](const std::string& e) {
@@ -365,11 +434,13 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
             if (sign_only[j]) {
               o << "const float sg = (w & 4) ? -1.f : 1.f;\n";
               for (int i = 0; i < NR; i++)
-                if ((i >> j) & 1) o << "v[" << i << "].x *= sg; v[" << i << "].y *= sg;\n";
+                if ((i >> j) & 1) o << RE(i) << " *= sg; " << IM(i) << " *= sg;\n";
             } else {
               o << "const float2 f = w8[w & 7];\n";
               for (int i = 0; i < NR; i++)
-                if ((i >> j) & 1) o << "v[" << i << "] = cmul(v[" << i << "], f);\n";
+                if ((i >> j) & 1)
+                  o << "{ const float2 a = cmul(make_float2(" << RE(i) << ", " << IM(i) << "), f); " << RE(i)
+                    << " = a.x; " << IM(i) << " = a.y; }\n";
             }
             o << "}\n";
           }
@@ -382,7 +453,17 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     }
     const bool last = s == d.n_stages - 1;
     const bool scale = last && d.post_scale != 1.0f;
-    if (kst) {
+    if (packed && kst) {
+      o << "{ float2 f = w8[kst & 7];\n";
+      if (scale) o << "f.x *= " << flit(d.post_scale) << "; f.y *= " << flit(d.post_scale) << ";\n";
+      o << "const float2 C2 = make_float2(f.x, f.x), S2 = make_float2(f.y, f.y), N2 = make_float2(-f.y, -f.y);\n"
+        << "#pragma unroll\nfor (int q = 0; q < " << NR / 2 << "; q++) { const float2 r = Vr[q], m = Vi[q]; "
+        << "Vr[q] = __ffma2_rn(r, C2, __fmul2_rn(m, N2)); Vi[q] = __ffma2_rn(r, S2, __fmul2_rn(m, C2)); } }\n";
+    } else if (packed && scale) {
+      o << "{ const float2 P2 = make_float2(" << flit(d.post_scale) << ", " << flit(d.post_scale) << ");\n"
+        << "#pragma unroll\nfor (int q = 0; q < " << NR / 2
+        << "; q++) { Vr[q] = __fmul2_rn(Vr[q], P2); Vi[q] = __fmul2_rn(Vi[q], P2); } }\n";
+    } else if (kst) {
       o << "{ float2 f = w8[kst & 7];\n";
       if (scale) o << "f.x *= " << flit(d.post_scale) << "; f.y *= " << flit(d.post_scale) << ";\n";
       o << "#pragma unroll\nfor (int i = 0; i < " << NR << "; i++) v[i] = cmul(v[i], f); }\n";
@@ -394,9 +475,12 @@ std::string gen_pass(const PassPlan& pp, const std::string& name) {
     if (j0 >= 0) {
       for (int i = 0; i < NR; i++) {
         if ((i >> j0) & 1) continue;
-        o << "*reinterpret_cast<float4*>(" << at(i) << ") = make_float4(v[" << i << "].x, v[" << i << "].y, v["
-          << (i | (1 << j0)) << "].x, v[" << (i | (1 << j0)) << "].y);\n";
+        const int i1 = i | (1 << j0);
+        o << "*reinterpret_cast<float4*>(" << at(i) << ") = make_float4(" << RE(i) << ", " << IM(i) << ", " << RE(i1)
+          << ", " << IM(i1) << ");\n";
       }
+    } else if (packed) {
+      for (int i = 0; i < NR; i++) o << "*(" << at(i) << ") = make_float2(" << RE(i) << ", " << IM(i) << ");\n";
     } else {
       for (int i = 0; i < NR; i++) o << "*(" << at(i) << ") = v[" << i << "];\n";
     }
@@ -506,7 +590,7 @@ void jit_prepare(Plan& p) {
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (PassPlan* pp : all) {
-      std::string src = gen_pass(*pp, kKernelName);
+      std::string src = gen_pass(*pp, kKernelName, p.opts.fp32x2 != 0);
       if (dump) {
         const std::string fn = std::string(dump) + "/pass_" + std::to_string(p.jit_entries.size()) + ".cu";
         if (FILE* f = std::fopen(fn.c_str(), "w")) {
@@ -549,7 +633,7 @@ void jit_prepare(Plan& p) {
   }
 }
 
-std::string jit_source(const PassPlan& pp) { return gen_pass(pp, kKernelName); }
+std::string jit_source(const PassPlan& pp) { return gen_pass(pp, kKernelName, true); }
 
 // Launch a pass with its specialised kernel; same launch shape as the
 // generic kernel.

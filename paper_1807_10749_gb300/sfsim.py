@@ -50,7 +50,8 @@ class sf_plan_opts(ctypes.Structure):
                 ("fuse_bits", ctypes.c_int32), ("exec_mode", ctypes.c_int32),
                 ("defer_last_level", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("batch_paths", ctypes.c_int32), ("run_bits", ctypes.c_int32),
-                ("jit", ctypes.c_int32), ("split_last", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("jit", ctypes.c_int32), ("split_last", ctypes.c_int32), ("fp32x2", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class sf_path_sel(ctypes.Structure):
