@@ -296,7 +296,7 @@ def main():
     ap.add_argument("--run-bits", type=int, default=0)
     ap.add_argument("--split-last", type=int, default=0, choices=[0, 1],
                     help="1: run the level before the folded last level as its own segment")
-    ap.add_argument("--fp32x2", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--fp32x2", type=int, default=0, choices=[0, 1],
                     help="1: packed FP32x2 arithmetic in the specialised kernels' Google-gate stages")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1],
                     help="1: per-pass specialised kernels compiled at plan time; 0: the generic pass kernel")

@@ -130,7 +130,6 @@ void sf_plan_opts_default(sf_plan_opts* o) {
   o->select_prefix_bits = -1;
   o->exec_mode = SF_EXEC_BATCHED;
   o->defer_last_level = 1;
-  o->fp32x2 = 1;
 }
 
 int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out) {

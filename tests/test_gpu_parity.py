@@ -29,10 +29,18 @@ def built():
     sim.build()
 
 
-@pytest.fixture(params=[0, 1], ids=["generic", "specialised"])
-def jit(request):
-    """Both pass-kernel forms: the generic kernel and the per-pass specialised
-    kernels compiled at plan time."""
+@pytest.fixture(params=[0, 1, 2], ids=["generic", "specialised", "specialised-fp32x2"])
+def jit(request, monkeypatch):
+    """The pass-kernel forms: the generic kernel, the per-pass specialised
+    kernels compiled at plan time, and those with packed FP32x2 stages."""
+    if request.param == 2:
+        orig = sfsim.Plan.__init__
+
+        def packed(self, text, **kw):
+            kw["fp32x2"] = 1
+            orig(self, text, **kw)
+        monkeypatch.setattr(sfsim.Plan, "__init__", packed)
+        return 1
     return request.param
 
 
@@ -46,6 +54,17 @@ def check_close(gpu, ref, n, label="", nonzero=True):
           f"rms|ref| = {rms:.3e}, rms|d| = {np.sqrt(np.mean(err ** 2)):.3e}")
     assert err.max() <= bound, f"{label}: {err.max()} > {bound}"
     assert err.max() <= REL_TOL * rms + 1e-300, f"{label}: {err.max()} > {REL_TOL} * rms {rms}"
+
+
+_REF_CACHE = {}
+
+
+def oracle_sf(setup_key, setup, ids, bits):
+    """The oracle's path sum, computed once per case for all kernel forms."""
+    key = (setup_key, np.asarray(ids, dtype=np.uint64).tobytes(), bits.tobytes())
+    if key not in _REF_CACHE:
+        _REF_CACHE[key] = sim.sf_amplitudes(setup, ids, bits)
+    return _REF_CACHE[key]
 
 
 def workload(name, **kw):
@@ -219,7 +238,7 @@ def test_6x7_path_list_matches_oracle(kind, split, jit):
     ids = np.unique(np.concatenate([ids, full]))
     if kind == "haar":
         ids = np.unique(np.concatenate([ids[:6], full[:40]]))
-    ref = sim.sf_amplitudes(setup, ids, bits)
+    ref = oracle_sf(("6x7", kind), setup, ids, bits)
     # split = 0: the level before the folded last level runs inside the last
     # program; split = 1: as its own segment with the node in between
     p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], split_last=split)
@@ -237,7 +256,7 @@ def test_7x8_path_list_matches_oracle(jit):
     setup = sim.SFSetup(c, w["side_b_mask"])
     bits = inputs.random_bitstrings(56, 1024, w["bitstring_seed"])
     ids = inputs.random_path_list(setup.x_bits, 2, 8)
-    ref = sim.sf_amplitudes(setup, ids, bits)
+    ref = oracle_sf(("7x8",), setup, ids, bits)
     p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
     check_close(amp, ref, 56, "7x8 2 paths")
