@@ -62,89 +62,24 @@ int cached_depths(const Plan& p) {
   return p.merged_last ? nL - 1 : nL;
 }
 
-uint64_t count_finals(const Plan& p, const std::vector<Range>& rs) {
-  const int fb = p.deferred ? p.defer_bits : 0;
-  uint64_t n = 0, last = ~0ull;
-  for (auto& r : rs) {
-    uint64_t a = r.lo >> fb, b = (r.hi - 1) >> fb;
-    n += b - a + 1;
-    if (a == last) n--;
-    last = b;
-  }
-  return n;
-}
-
-// Bits of a final's id above its parent at depth nc - 1.
-int final_shift(const Plan& p) {
-  const int nL = (int)p.levels.size();
-  if (p.merged_last) return nL >= 2 ? p.levels[nL - 2].bits : 0;
-  if (!p.deferred) return nL > 0 ? p.levels[nL - 1].bits : 0;
-  return 0;
-}
-
-// The block size B (finals per block) and per-depth slot capacities. The
-// default block holds ~2^26 amplitudes of finals and at least one level's
-// fan-out, so that siblings (finals of one parent) share their launches and
-// read the parent's tiles once. A depth needs as many slots as the most
-// distinct ancestors any block of B consecutive finals has there: counted on
-// the selection when it has at most 2^20 finals, else the bound min(B, 2^bits).
-// B halves until the nodes fit the device budget.
-Layout make_layout(const Plan& p, const std::vector<Range>& rs, int64_t budget_override = 0) {
-  const int nc = cached_depths(p);
+Layout make_layout(const Plan& p, uint64_t n_finals, int64_t budget_override = 0) {
+  const int nL = cached_depths(p);
   const size_t nb = node_bytes(p);
-  const uint64_t n_finals = count_finals(p, rs);
   int64_t budget = budget_override > 0 ? budget_override : p.opts.hbm_budget_bytes;
   const size_t amps = ((size_t)1 << p.A.m) + ((size_t)1 << p.B.m);
-  int max_bits = 0;
-  for (const auto& l : p.levels) max_bits = std::max(max_bits, l.bits);
-  int64_t B = p.opts.batch_paths > 0
-                  ? p.opts.batch_paths
-                  : std::max<int64_t>({1, ((int64_t)1 << 26) / (int64_t)amps, (int64_t)1 << std::min(max_bits, 4)});
+  int64_t B = p.opts.batch_paths > 0 ? p.opts.batch_paths : std::max<int64_t>(1, ((int64_t)1 << 26) / (int64_t)amps);
   B = std::min<int64_t>(B, std::max<uint64_t>(1, n_finals));
-  // the selection's finals in order (small selections only)
-  std::vector<uint64_t> fids;
-  if (n_finals <= (1u << 20)) {
-    const int fb = p.deferred ? p.defer_bits : 0;
-    uint64_t last = ~0ull;
-    for (const auto& r : rs) {
-      if (r.hi <= r.lo) continue;
-      for (uint64_t f = r.lo >> fb; f <= (r.hi - 1) >> fb; f++)
-        if (f != last || fids.empty()) {
-          fids.push_back(f);
-          last = f;
-        }
-    }
-  }
-  const int sh_f = final_shift(p);
-  const int tb_last = nc > 0 ? total_bits_below(p, nc - 1) : 0;
   Layout lay;
   while (true) {
-    lay.cap.assign(std::max(0, nc), 0);
-    if (!fids.empty()) {
-      for (size_t b0 = 0; b0 < fids.size(); b0 += (size_t)B) {
-        const size_t b1 = std::min(fids.size(), b0 + (size_t)B);
-        for (int d = 0; d < nc; d++) {
-          const int below = total_bits_below(p, d) - tb_last;
-          int distinct = 0;
-          uint64_t prev = ~0ull;
-          for (size_t i = b0; i < b1; i++) {
-            const uint64_t pid = fids[i] >> sh_f;
-            const uint64_t id = below >= 64 ? 0 : (pid >> below);
-            if (i == b0 || id != prev) distinct++;
-            prev = id;
-          }
-          lay.cap[d] = std::max(lay.cap[d], distinct);
-        }
-      }
-    } else {
-      int cum = 0;
-      for (int d = 0; d < nc; d++) {
-        lay.cap[d] = (int)((cum >= 62) ? B : std::min<int64_t>(B, (int64_t)1 << cum));
-        cum += p.levels[d].bits;
-      }
-    }
+    lay.cap.assign(std::max(0, nL), 0);
     size_t tot = (size_t)B;
-    for (int c : lay.cap) tot += (size_t)c;
+    int cum = 0;
+    for (int s = 0; s < nL; s++) {
+      int64_t c = (cum >= 62) ? B : std::min<int64_t>(B, (int64_t)1 << cum);
+      lay.cap[s] = (int)c;
+      tot += (size_t)c;
+      if (s < nL) cum += p.levels[s].bits;
+    }
     if ((int64_t)(tot * nb) <= budget || B == 1) {
       lay.B = (int)B;
       lay.total_slots = tot;
@@ -155,6 +90,18 @@ Layout make_layout(const Plan& p, const std::vector<Range>& rs, int64_t budget_o
     }
     B = std::max<int64_t>(1, B / 2);
   }
+}
+
+uint64_t count_finals(const Plan& p, const std::vector<Range>& rs) {
+  const int fb = p.deferred ? p.defer_bits : 0;
+  uint64_t n = 0, last = ~0ull;
+  for (auto& r : rs) {
+    uint64_t a = r.lo >> fb, b = (r.hi - 1) >> fb;
+    n += b - a + 1;
+    if (a == last) n--;
+    last = b;
+  }
+  return n;
 }
 
 void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan, int* err) {
@@ -277,7 +224,7 @@ size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int6
   (void)n;
   double fa;
   auto rs = select_ranges(p, s, &fa);
-  Layout lay = make_layout(p, rs, budget);
+  Layout lay = make_layout(p, count_finals(p, rs), budget);
   return lay.total_slots * node_bytes(p) + 256;
 }
 
@@ -350,7 +297,8 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
     if (prof) prof_end(plan, e1, st);
   }
   if (n == 0 || rs.empty()) return;
-  Layout lay = make_layout(plan, rs, budget);
+  const uint64_t nfin = count_finals(plan, rs);
+  Layout lay = make_layout(plan, nfin, budget);
   const size_t nb = node_bytes(plan);
   const size_t need = lay.total_slots * nb + 256;
   if (!ws || ws_bytes < need)
@@ -382,7 +330,9 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   // nc cached depths 0 .. nc-1; a final's parent is its node at depth nc-1,
   // sh_f path bits (of the final id) above it
   const int nc = cached_depths(plan);
-  const int sh_f = final_shift(plan);
+  int sh_f = 0;
+  if (plan.merged_last) sh_f = nL >= 2 ? plan.levels[nL - 2].bits : 0;
+  else if (!plan.deferred) sh_f = nL > 0 ? plan.levels[nL - 1].bits : 0;
   const SegmentPlan& finA =
       plan.merged_last ? plan.A.last_merged : (plan.deferred ? plan.A.last_deferred : plan.A.seg[nL]);
   const SegmentPlan& finB =
