@@ -123,22 +123,23 @@ def test_feistel_matches_oracle_at_28_bits():
     p.close()
 
 
-@pytest.mark.parametrize("name", ["4x4_d10", "6x7_d26", "7x8_d40"])
-def test_specialised_pass_kernels_compile(name):
+@pytest.mark.parametrize("name,packed", [("4x4_d10", 0), ("6x7_d26", 0), ("7x8_d40", 0), ("7x8_d40", 1)])
+def test_specialised_pass_kernels_compile(name, packed):
     """Every pass of the plan compiles into its own kernel (NVRTC runs
-    without a GPU); a second plan of the same circuit reuses the binaries."""
+    without a GPU), scalar or with packed FP32x2 stages; a second plan of the
+    same circuit reuses the binaries."""
     import time
     w = inputs.WORKLOADS[name]
     text = inputs.workload_circuit(name).text()
     try:
-        p = sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=1)
+        p = sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=1, fp32x2=packed)
     except sfsim.SFError as e:
         if e.code == sfsim.SF_EUNSUPPORTED:
             pytest.skip(str(e))
         raise
     p.close()
     t = time.perf_counter()
-    q = sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=1)
+    q = sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=1, fp32x2=packed)
     assert time.perf_counter() - t < 2.0   # cached
     q.close()
     with pytest.raises(sfsim.SFError):
