@@ -191,3 +191,45 @@ def test_cost_fit_recovers_coefficients():
     assert got2[2] == 0.0 and np.allclose(got2[[0, 1, 3]], [1e-4, 2e-12, 5e-10], rtol=1e-8)
     with pytest.raises(sfsim.SFError):
         sfsim.sf_cost_fit(T, -secs)
+
+
+def _final_bytes(p):
+    nL = sfsim.sf_plan_info(p.handle)["n_levels"]
+    return sum(sfsim.sf_plan_segment_stats(p.handle, h, nL + 1)[2] for h in (0, 1))
+
+
+def test_merged_last_program_moves_fewer_bytes():
+    """With the last level folded into the gather, planning the level before
+    it and the last segment as one program saves the node in between: at 7x8
+    the merged final moves fewer bytes than the two programs together."""
+    w = inputs.WORKLOADS["7x8_d40"]
+    text = inputs.workload_circuit("7x8_d40").text()
+    merged = sfsim.Plan(text, side_b_mask=w["side_b_mask"])
+    split = sfsim.Plan(text, side_b_mask=w["side_b_mask"], split_last=1)
+    nL = sfsim.sf_plan_info(split.handle)["n_levels"]
+    split_bytes = _final_bytes(split) + sum(sfsim.sf_plan_segment_stats(split.handle, h, nL - 1)[2]
+                                            for h in (0, 1))
+    assert _final_bytes(merged) < 0.6 * split_bytes
+    merged.close()
+    split.close()
+
+
+def test_automatic_tiles_and_runs_move_no_more_bytes_than_fixed_small_tiles():
+    """Per segment the planner keeps the (tile, run) candidate of least
+    estimated time, bytes over the tile size's HBM fraction (0.75 at 2^12,
+    0.64 at 2^13). A 2^13 tile wins only with under 0.85x the bytes of the
+    best 2^12 candidate and the runs tie on efficiency, so every segment, and
+    the whole plan, moves no more bytes than with 2^12 tiles and either run
+    width."""
+    w = inputs.WORKLOADS["7x8_d40"]
+    text = inputs.workload_circuit("7x8_d40").text()
+
+    def total(p):
+        nL = sfsim.sf_plan_info(p.handle)["n_levels"]
+        t = sum(sfsim.sf_plan_segment_stats(p.handle, h, s)[2]
+                for h in (0, 1) for s in list(range(nL - 1)) + [nL + 1])
+        p.close()
+        return t
+    auto = total(sfsim.Plan(text, side_b_mask=w["side_b_mask"]))
+    for rb in (3, 4):
+        assert auto <= total(sfsim.Plan(text, side_b_mask=w["side_b_mask"], tile_bits=12, run_bits=rb))
