@@ -5,8 +5,8 @@ CPU-baseline leg (and its reference arm) may import or run this package. The
 CUDA library never calls it and shares no code with it.
 
 What it computes, plainly and slowly, in complex128:
-  * sv_amplitudes  - full state-vector simulation (Section 2, "Schroedinger-style
-    simulation"), one dense 2x2 / 4x4 gate at a time, in circuit order;
+  * sv_amplitudes  - full state-vector (Schroedinger) simulation (Section 2),
+    one dense 2x2 / 4x4 gate at a time, in circuit order;
   * dense_amplitudes - brute force: every gate as a 2^n x 2^n matrix built from
     Kronecker products (n <= 10);
   * sf_amplitudes  - the Schroedinger-Feynman path sum of Eq. 2 (and its

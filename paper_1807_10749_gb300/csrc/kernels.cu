@@ -6,8 +6,8 @@
 //                  register stages; a stage gives every thread 2^R amplitudes
 //                  whose R "register bits" vary, applies the stage's gates in
 //                  registers, and writes them back. Gates: the Google gates in
-//                  their multiplication-free integer form (Section 2: "no
-//                  floating-point multiplications except for T"), general 2x2
+//                  their multiplication-free integer form (Section 2: only the
+//                  T gates need floating-point multiplications), general 2x2
 //                  and 4x4 matrices, per-path cross-gate factors (Eq. 1 and
 //                  Section 7), and groups of diagonal gates applied as one
 //                  mod-8 power of e^{i pi/4} computed from bitmasks (Section 2:
