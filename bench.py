@@ -33,13 +33,20 @@ METRIC = "simulated paths/s at 7x8 depth 1+40+1"
 UNIT = "paths/s"
 
 
-def config_dict(n_bits, extra=None):
-    d = {"workload": "7x8 grid, depth 1+40+1 (v2 one-qubit rule), cut cols 0-3 | 4-7 (28+28 qubits), 35 cut CZs, "
-                     "f = 0.5% (FRACTION, 28 prefix bits, seed 7), 1M random bitstrings; "
-                     "step = one 128-path prefix subtree",
-         "grid": "7x8", "depth": "1+40+1", "fidelity": FIDELITY, "bitstrings": n_bits,
-         "paths_per_step": 128,
-         "l2": "no flush: every pass streams 2 GiB half-states, far larger than the 129 MB L2"}
+def config_dict(n_bits, extra=None, workload=WORKLOAD):
+    if workload == "5x10_d16":
+        d = {"workload": "5x10 grid, depth 1+16+1 (v2 one-qubit rule), cut 25+25 qubits, f = 0.5% "
+                         "(FRACTION, seed 7), random bitstrings; step = one 128-path prefix subtree "
+                         "(the profiling case: 256 MB half-states, above the 129 MB L2)",
+             "grid": "5x10", "depth": "1+16+1", "fidelity": FIDELITY, "bitstrings": n_bits,
+             "paths_per_step": 128}
+    else:
+        d = {"workload": "7x8 grid, depth 1+40+1 (v2 one-qubit rule), cut cols 0-3 | 4-7 (28+28 qubits), "
+                         "35 cut CZs, f = 0.5% (FRACTION, 28 prefix bits, seed 7), 1M random bitstrings; "
+                         "step = one 128-path prefix subtree",
+             "grid": "7x8", "depth": "1+40+1", "fidelity": FIDELITY, "bitstrings": n_bits,
+             "paths_per_step": 128,
+             "l2": "no flush: every pass streams 2 GiB half-states, far larger than the 129 MB L2"}
     if extra:
         d.update(extra)
     return d
@@ -448,14 +455,13 @@ def main():
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": config_dict(len(bits), {"exec_mode": args.exec_mode, "f_actual": f_actual,
-                                              "tile_bits": args.tile_bits or "per segment (12 or 13)", "fuse_bits": args.fuse_bits or 5,
-                                              "run_bits": args.run_bits or "per segment (3 or 4)",
-                                              "pass_kernels": "specialised" if args.jit else "generic",
-                                              "split_last": args.split_last, "fp32x2": args.fp32x2,
-                                              "plan_seconds": t_plan,
-                                              "paths_selected": n_sel, "parallelism": f"paths x{world}",
-                                              "wall_s": wall}),
+            "config": config_dict(len(bits), workload=args.workload, extra={
+                "exec_mode": args.exec_mode, "f_actual": f_actual,
+                "tile_bits": args.tile_bits or "per segment (12 or 13)", "fuse_bits": args.fuse_bits or 5,
+                "run_bits": args.run_bits or "per segment (3 or 4)",
+                "pass_kernels": "specialised" if args.jit else "generic",
+                "split_last": args.split_last, "fp32x2": args.fp32x2, "plan_seconds": t_plan,
+                "paths_selected": n_sel, "parallelism": f"paths x{world}", "wall_s": wall}),
             "roofline": {"kernel": ("sf_pass_spec (per-pass specialised fused tile pass)" if args.jit
                                     else "pass_kernel (generic fused tile pass)"), "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
