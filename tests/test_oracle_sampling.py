@@ -67,3 +67,25 @@ def test_validation_protocol_oracle():
     other = sim.sv_amplitudes(circuit.parse(inputs.google_circuit(4, 4, 32, 6).text()), xs)
     assert validation.fidelity_estimate(other[k], ver[k]) < 0.01
     assert not validation.protocol_passes(other[k], ver[k], f1, 0.02)
+
+
+def test_fidelity_estimate_pins():
+    """f_e = |<a|b>|^2 / (<a|a><b|b>) (Appendix C): invariant under complex
+    scaling of either argument, symmetric, within [0, 1] (Cauchy-Schwarz), 0
+    for orthogonal vectors, and a hand value: a = (1, i), b = (1, 1) gives
+    |1 - i|^2 / (2 * 2) = 1/2."""
+    from oracle import validation
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        a = rng.normal(size=64) + 1j * rng.normal(size=64)
+        b = rng.normal(size=64) + 1j * rng.normal(size=64)
+        c = complex(rng.normal(), rng.normal())
+        f = validation.fidelity_estimate(a, b)
+        assert 0.0 <= f <= 1.0
+        assert abs(validation.fidelity_estimate(b, a) - f) < 1e-12
+        assert abs(validation.fidelity_estimate(c * a, b) - f) < 1e-12
+        assert abs(validation.fidelity_estimate(a, c * a) - 1.0) < 1e-12
+    assert validation.fidelity_estimate(np.array([1, 0]), np.array([0, 1j])) == 0.0
+    assert abs(validation.fidelity_estimate(np.array([1, 1j]), np.array([1, 1])) - 0.5) < 1e-15
+    re, im, na, nb = validation.overlap_sums(np.array([1, 1j]), np.array([1, 1]))
+    assert (re, im, na, nb) == (1.0, -1.0, 2.0, 2.0)   # <a|b> = 1 - i
