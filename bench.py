@@ -320,6 +320,8 @@ def main():
                     help="1: run the level before the folded last level as its own segment")
     ap.add_argument("--fp32x2", type=int, default=0, choices=[0, 1],
                     help="1: packed FP32x2 arithmetic in the specialised kernels' Google-gate stages")
+    ap.add_argument("--dense-finals", type=int, default=0, choices=[0, 1],
+                    help="1: the final programs write whole final states (no compact blocks)")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1],
                     help="1: per-pass specialised kernels compiled at plan time; 0: the generic pass kernel")
     args = ap.parse_args()
@@ -353,7 +355,7 @@ def main():
     t_plan = time.perf_counter()
     plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode, tile_bits=args.tile_bits,
                       fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit,
-                      split_last=args.split_last, fp32x2=args.fp32x2)
+                      split_last=args.split_last, fp32x2=args.fp32x2, dense_finals=args.dense_finals)
     t_plan = time.perf_counter() - t_plan
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
@@ -460,7 +462,11 @@ def main():
                 "tile_bits": args.tile_bits or "per segment (12 or 13)", "fuse_bits": args.fuse_bits or 5,
                 "run_bits": args.run_bits or "per segment (3 or 4)",
                 "pass_kernels": "specialised" if args.jit else "generic",
-                "split_last": args.split_last, "fp32x2": args.fp32x2, "plan_seconds": t_plan,
+                "split_last": args.split_last, "fp32x2": args.fp32x2,
+                "finals": ("dense (whole final states written)" if args.dense_finals else
+                           "compact where the planner allows (only the 2^g-amplitude blocks of "
+                           "requested bitstrings written)"),
+                "plan_seconds": t_plan,
                 "paths_selected": n_sel, "parallelism": f"paths x{world}", "wall_s": wall}),
             "roofline": {"kernel": ("sf_pass_spec (per-pass specialised fused tile pass)" if args.jit
                                     else "pass_kernel (generic fused tile pass)"), "bound": "hbm",

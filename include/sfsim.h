@@ -120,7 +120,14 @@ typedef struct {
                                H, X^1/2, Y^1/2 and phase groups hold amplitude
                                pairs in FP32x2 registers (packed adds), 0 = scalar
                                (default; measured 3% faster on the 7x8 workload) */
-  int32_t reserved[3];
+  int32_t dense_finals;     /* with the last level folded into the gather: 0 = the
+                               last pass of each half's final program writes only
+                               the blocks of 2^g amplitudes (g = cut gates of the
+                               folded level) that hold a requested bitstring, into
+                               a compact buffer, when that is at most a quarter of
+                               the half and fits the budget; 1 = always write the
+                               whole final state */
+  int32_t reserved[2];
 } sf_plan_opts;
 
 SF_API void sf_plan_opts_default(sf_plan_opts* o);

@@ -59,11 +59,12 @@ void ensure_device(sf::Plan& p) {
     cuda_check(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
     p.opts.hbm_budget_bytes = (int64_t)(fr / 4 * 3);
   }
-  uint32_t *a = nullptr, *b = nullptr;
+  uint32_t *a = nullptr, *b = nullptr, *cnt = nullptr;
   int* e = nullptr;
   try {
     cuda_check(cudaMalloc(&e, sizeof(int)), "cudaMalloc");
     cuda_check(cudaMemset(e, 0, sizeof(int)), "cudaMemset");
+    cuda_check(cudaMalloc(&cnt, 2 * sf::kCountRing * sizeof(uint32_t)), "cudaMalloc");
     cuda_check(cudaMalloc(&a, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
     cuda_check(cudaMalloc(&b, 8 * 256 * sizeof(uint32_t)), "cudaMalloc");
     cuda_check(cudaMemcpy(a, p.A.tab.data(), 8 * 256 * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
@@ -72,9 +73,11 @@ void ensure_device(sf::Plan& p) {
     if (a) cudaFree(a);
     if (b) cudaFree(b);
     if (e) cudaFree(e);
+    if (cnt) cudaFree(cnt);
     throw;
   }
   p.d_err = e;
+  p.d_cnt = cnt;
   p.d_tabA = a;
   p.d_tabB = b;
 }
@@ -151,6 +154,7 @@ int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out)
     o.batch_paths = 1;
   }
   if (o.jit != 0 && o.jit != 1) sf::fail(SF_EINVAL, "jit must be 0 or 1");
+  if (o.dense_finals != 0 && o.dense_finals != 1) sf::fail(SF_EINVAL, "dense_finals must be 0 or 1");
   sf::Plan* p = sf::plan_create(c->c, o);
   if (o.jit) {
     try {
@@ -251,6 +255,7 @@ void sf_plan_destroy(sf_plan* h) {
   if (h->p) {
     sf::prof_release(*h->p);
     if (h->p->d_err) cudaFree(h->p->d_err);
+    if (h->p->d_cnt) cudaFree(h->p->d_cnt);
     if (h->p->d_tabA) cudaFree(h->p->d_tabA);
     if (h->p->d_tabB) cudaFree(h->p->d_tabB);
     sf::plan_destroy(h->p);

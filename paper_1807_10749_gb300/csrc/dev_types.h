@@ -128,10 +128,34 @@ struct PassLaunch {
   uint8_t xshift[MAX_CROSS];
   uint8_t xbits[MAX_CROSS];
   int* err;        // set to 1 if a bounded wait gave up
+  // Compact output (final passes whose result only the gather reads): null =
+  // every live amplitude is written at its index. Otherwise only requested
+  // parts are written. A part is a tile's share of one block of the gather
+  // (2^ctl consecutive tile elements: positions 0..ctl-1); parts are numbered
+  // tile-major, P = tile * 2^(k-ctl) + u for part u of the tile, and part P
+  // goes to out + slot(P) * 2^ctl, slot(P) = requested parts below P. cmap
+  // holds per 32 parts the pair (bitmap word, requested parts in earlier
+  // words), so a tile's parts are consecutive bits of the map.
+  const uint32_t* cmap;
+  int32_t ctl;
+  int32_t cpad;
   int32_t n_nodes;
   PassNode nodes[MAX_NODES];
 };
 
+
+// The bits of x at the set positions of mask, packed from bit 0 up in
+// ascending position order.
+SF_HD inline uint32_t pext32(uint32_t x, uint32_t mask) {
+  uint32_t r = 0, b = 1;
+  while (mask) {
+    const uint32_t low = mask & (0u - mask);
+    if (x & low) r |= b;
+    b <<= 1;
+    mask ^= low;
+  }
+  return r;
+}
 
 // Shared-memory layout of a tile: element e lives at swz(e), a linear XOR
 // swizzle that folds index bits 4..12 into bits 1..3. It keeps 16-byte

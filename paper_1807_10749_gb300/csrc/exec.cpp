@@ -48,11 +48,95 @@ int total_bits_below(const Plan& p, int depth) {  // bits of levels[depth .. nL-
   return b;
 }
 
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Compact finals. With the last level folded into the gather, the gather
+// reads from each final only the blocks of 2^g amplitudes (the g cut qubits
+// of the folded level sit at layout positions 0..g-1) that hold a requested
+// bitstring. The last pass of a half's final program then writes just those
+// blocks' parts (a part is a tile's share of a block: positions 0..ctl-1 of
+// the tile), into a compact buffer, when that buffer is at most a quarter of
+// the half. The parts are numbered tile-major (PassLaunch::cmap), so a tile
+// reads its stretch of the part map with one coalesced load. A half
+// qualifies when that pass has no output pins (every tile is written, none
+// pinned away), its lowest ctl >= 1 tile bits are positions 0..ctl-1 and a
+// block spans at most two parts (g - ctl <= 1).
+struct CompactSide {
+  bool on = false;
+  CompactMap c{};    // without the map pointer
+  size_t nw = 0;     // map words (32 parts each)
+  size_t cap = 0;    // slots per final: min(parts of n blocks, parts)
+  size_t map_bytes = 0, sums_bytes = 0, buf_bytes = 0;
+};
+struct Compact {
+  int g = 0;
+  CompactSide s[2];
+  size_t fixed = 0;      // maps and chunk counts
+  size_t per_final = 0;  // compact buffers of one final, both halves
+  bool any() const { return s[0].on || s[1].on; }
+};
+
+const SegmentPlan& final_segment(const Plan& p, int side) {
+  const HalfPlan& H = side ? p.B : p.A;
+  return p.merged_last ? H.last_merged : (p.deferred ? H.last_deferred : H.seg[p.levels.size()]);
+}
+
+Compact compact_plan(const Plan& p, int64_t n) {
+  Compact c;
+  if (!p.deferred || p.opts.dense_finals || n <= 0 || p.levels.empty()) return c;
+  const Level& lv = p.levels.back();
+  const int g = lv.n_cross;
+  if (g < 1 || g > MAX_DEFER) return c;
+  c.g = g;
+  for (int side = 0; side < 2; side++) {
+    const HalfPlan& H = side ? p.B : p.A;
+    const SegmentPlan& fin = final_segment(p, side);
+    CompactSide& cs = c.s[side];
+    if (fin.passes.empty() || !fin.pins_out.empty() || H.m <= g || H.m > 32) continue;
+    const DevPass& d = fin.passes.back().dev;
+    if (d.n_pin_out != 0 || d.n_free != H.m - d.k) continue;
+    uint32_t dmask = 0;
+    for (int t = 0; t < g; t++) {
+      const CrossGate& x = p.cross[lv.first_cross + t];
+      const int pos = H.pos_of[side ? x.qb : x.qa];
+      if (pos >= 0 && pos < 32) dmask |= 1u << pos;
+    }
+    if (dmask != (1u << g) - 1u) continue;
+    int tl = 0;
+    while (tl < d.k && d.gpos[tl] < g) {
+      if (d.gpos[tl] != tl) break;
+      tl++;
+    }
+    if (tl < 1 || (tl < d.k && d.gpos[tl] < g) || g - tl > 1) continue;
+    uint32_t active = 0;
+    for (int j = 0; j < d.k; j++) active |= 1u << d.gpos[j];
+    const uint32_t all = H.m == 32 ? 0xffffffffu : ((1u << H.m) - 1u);
+    cs.c.cfree = all & ~active;
+    cs.c.cpart = active & ~((1u << tl) - 1u);
+    cs.c.ckt = d.k - tl;
+    cs.c.ctl = tl;
+    cs.c.csub1 = g > tl ? (pext32(1u << tl, cs.c.cfree) << cs.c.ckt) : 0u;
+    const size_t parts = (size_t)1 << (H.m - tl);
+    cs.cap = std::min<size_t>((size_t)n * (g > tl ? 2 : 1), parts);
+    if ((cs.cap << tl) * 4 > ((size_t)1 << H.m)) continue;
+    cs.on = true;
+    cs.nw = (parts + 31) / 32;
+    cs.map_bytes = align256(cs.nw * 8);
+    cs.sums_bytes = align256(((cs.nw + 2047) / 2048) * 4);
+    cs.buf_bytes = align256((cs.cap << tl) * 8);
+    c.fixed += cs.map_bytes + cs.sums_bytes;
+    c.per_final += cs.buf_bytes;
+  }
+  return c;
+}
+
 // The block size (finals per block) and per-depth slot capacities.
 struct Layout {
   int B = 1;
   std::vector<int> cap;
   size_t total_slots = 0;
+  bool compact = false;  // finals written as compact blocks (Compact)
+  size_t bytes = 0;      // workspace bytes after alignment of its base
 };
 
 // Depths whose nodes are cached: all levels, except that the finals of a
@@ -62,7 +146,7 @@ int cached_depths(const Plan& p) {
   return p.merged_last ? nL - 1 : nL;
 }
 
-Layout make_layout(const Plan& p, uint64_t n_finals, int64_t budget_override = 0) {
+Layout make_layout(const Plan& p, uint64_t n_finals, const Compact& cp, int64_t budget_override = 0) {
   const int nL = cached_depths(p);
   const size_t nb = node_bytes(p);
   int64_t budget = budget_override > 0 ? budget_override : p.opts.hbm_budget_bytes;
@@ -80,11 +164,17 @@ Layout make_layout(const Plan& p, uint64_t n_finals, int64_t budget_override = 0
       tot += (size_t)c;
       if (s < nL) cum += p.levels[s].bits;
     }
-    if ((int64_t)(tot * nb) <= budget || B == 1) {
+    // compact finals when they fit: smaller blocks first, dense finals last
+    const size_t dense = tot * nb;
+    const size_t withc = align256(dense) + cp.fixed + (size_t)B * cp.per_final;
+    const bool fits_c = cp.any() && (int64_t)withc <= budget;
+    if (fits_c || (!cp.any() && (int64_t)dense <= budget) || B == 1) {
       lay.B = (int)B;
       lay.total_slots = tot;
-      if ((int64_t)(tot * nb) > budget)
-        fail(SF_ENOMEM, "device memory budget too small for one path (" + std::to_string(tot * nb) +
+      lay.compact = fits_c;
+      lay.bytes = fits_c ? withc : dense;
+      if ((int64_t)lay.bytes > budget)
+        fail(SF_ENOMEM, "device memory budget too small for one path (" + std::to_string(dense) +
                             " bytes needed)");
       return lay;
     }
@@ -111,6 +201,8 @@ void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan, int* err) 
     fail(SF_EUNSUPPORTED, "internal: pass program too large");
   L.pass = pp.dev;
   L.err = err;
+  L.cmap = nullptr;
+  L.ctl = L.cpad = 0;
   std::copy(pp.stages.begin(), pp.stages.end(), L.stages);
   std::copy(pp.ops.begin(), pp.ops.end(), L.ops);
   std::copy(pp.phases.begin(), pp.phases.end(), L.phases);
@@ -159,8 +251,9 @@ struct Job {
 
 // Algorithmic bytes of one pass launch: live input amplitudes read (unless
 // generated) once per distinct input buffer, plus live output amplitudes
-// written per node, 8 bytes each.
-double pass_bytes(const DevPass& d, int nodes, int inputs) {
+// written per node (unless the writes are compact: counted on the device),
+// 8 bytes each.
+double pass_bytes(const DevPass& d, int nodes, int inputs, bool dense_out = true) {
   uint32_t active = 0;
   for (int j = 0; j < d.k; j++) active |= 1u << d.gpos[j];
   uint32_t pin_in = 0, pin_out = 0;
@@ -169,14 +262,24 @@ double pass_bytes(const DevPass& d, int nodes, int inputs) {
   const double tiles = std::ldexp(1.0, d.n_free);
   const double rd = d.gen_input ? 0.0 : tiles * std::ldexp(1.0, d.k - __builtin_popcount(pin_in & active));
   const double wr = tiles * std::ldexp(1.0, d.k - __builtin_popcount(pin_out & active));
-  return 8.0 * (rd * inputs + wr * nodes);
+  return 8.0 * (rd * inputs + (dense_out ? wr * nodes : 0.0));
 }
+
+// The compact output of a final program's last pass (per job: its buffer).
+struct CompactOut {
+  const uint32_t* cmap = nullptr;
+  int ctl = 0;
+  const uint32_t* count = nullptr;  // device count of marked parts (profile)
+  std::vector<void*> out;
+};
 
 // Run a segment program for a batch of nodes of one half.
 void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<Job>& jobs,
-                 cudaStream_t st, bool prof, int* err) {
+                 cudaStream_t st, bool prof, int* err, const CompactOut* co = nullptr) {
   if (jobs.empty()) return;
+  if (co && co->out.size() != jobs.size()) fail(SF_EINVAL, "internal: compact outputs");
   for (size_t p = 0; p < seg.passes.size(); p++) {
+    const bool compact = co && p + 1 == seg.passes.size();
     const PassPlan& pp = seg.passes[p];
     static thread_local std::unique_ptr<PassLaunch> scratch;
     if (!scratch) {
@@ -185,13 +288,17 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
     }
     PassLaunch* L = scratch.get();
     fill_launch(*L, pp, plan, err);
+    if (compact) {
+      L->cmap = co->cmap;
+      L->ctl = co->ctl;
+    }
     const int tiles = 1 << pp.dev.n_free;
     for (size_t j0 = 0; j0 < jobs.size(); j0 += MAX_NODES) {
       size_t j1 = std::min(jobs.size(), j0 + MAX_NODES);
       L->n_nodes = (int)(j1 - j0);
       for (size_t j = j0; j < j1; j++) {
         L->nodes[j - j0].in = (p == 0) ? jobs[j].in : jobs[j].out;
-        L->nodes[j - j0].out = jobs[j].out;
+        L->nodes[j - j0].out = compact ? co->out[j] : jobs[j].out;
         L->nodes[j - j0].path = jobs[j].path;
       }
       void* e1 = nullptr;
@@ -203,7 +310,9 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
         for (int j = 0; j < L->n_nodes; j++) ins.push_back({L->nodes[j].in, pin_key(pp.dev, plan, L->nodes[j].path)});
         std::sort(ins.begin(), ins.end());
         const int uniq = (int)(std::unique(ins.begin(), ins.end()) - ins.begin());
-        prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes, uniq), st, &e1);
+        prof_begin(plan, 0, pass_bytes(pp.dev, L->n_nodes, uniq, !compact), st, &e1);
+        if (compact && co->count)
+          plan.prof.units.push_back({0, co->count, (double)L->n_nodes * (8.0 * (double)(1u << co->ctl))});
       }
       if (pp.jit_id >= 0) launch_pass_jit(*L, tiles, plan.jit_entries[pp.jit_id], st);
       else launch_pass(*L, tiles, plan.fuse_bits, plan.tile_bits, st);
@@ -221,15 +330,14 @@ double segment_bytes(const SegmentPlan& s) {
 }
 
 size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget) {
-  (void)n;
   double fa;
   auto rs = select_ranges(p, s, &fa);
-  Layout lay = make_layout(p, count_finals(p, rs), budget);
-  return lay.total_slots * node_bytes(p) + 256;
+  Layout lay = make_layout(p, count_finals(p, rs), compact_plan(p, n), budget);
+  return lay.bytes + 256;
 }
 
-void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out) {
-  p.prof.launches[kind]++;
+void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out, int launches) {
+  p.prof.launches[kind] += launches;
   p.prof.bytes[kind] += bytes;
   *e1_out = nullptr;
   if (!p.prof.timing) return;
@@ -261,6 +369,13 @@ void prof_collect(Plan& p) {
     p.prof.pool.push_back(r.e1);
   }
   p.prof.pending.clear();
+  // the counters are written by kernels on the callers' streams
+  if (!p.prof.units.empty()) cudaDeviceSynchronize();
+  for (auto& u : p.prof.units) {
+    uint32_t v = 0;
+    if (cudaMemcpy(&v, u.count, sizeof(v), cudaMemcpyDeviceToHost) == cudaSuccess) p.prof.bytes[u.kind] += v * u.unit;
+  }
+  p.prof.units.clear();
 }
 
 void prof_release(Plan& p) {
@@ -298,9 +413,10 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   }
   if (n == 0 || rs.empty()) return;
   const uint64_t nfin = count_finals(plan, rs);
-  Layout lay = make_layout(plan, nfin, budget);
+  const Compact cp = compact_plan(plan, n);
+  Layout lay = make_layout(plan, nfin, cp, budget);
   const size_t nb = node_bytes(plan);
-  const size_t need = lay.total_slots * nb + 256;
+  const size_t need = lay.bytes + 256;
   if (!ws || ws_bytes < need)
     fail(SF_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~(uintptr_t)255);
@@ -338,6 +454,51 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   const SegmentPlan& finB =
       plan.merged_last ? plan.B.last_merged : (plan.deferred ? plan.B.last_deferred : plan.B.seg[nL]);
 
+  // compact finals: block maps after the node slots, then B finals' buffers;
+  // the maps are built once per call from the bitstrings
+  uint32_t* cmap[2] = {nullptr, nullptr};
+  char* cfin = nullptr;
+  const uint32_t* ccount[2] = {nullptr, nullptr};
+  if (lay.compact) {
+    char* at = base + align256(lay.total_slots * nb);
+    BlockMapLaunch M;
+    std::memset(&M, 0, sizeof(M));
+    M.tab[0] = tabA;
+    M.tab[1] = tabB;
+    M.bits = d_bits;
+    M.n = n;
+    uint32_t* cnt = nullptr;
+    if (prof && plan.d_cnt) {
+      if (plan.cnt_seq > 0 && plan.cnt_seq % kCountRing == 0) prof_collect(plan);
+      cnt = plan.d_cnt + 2 * (plan.cnt_seq % kCountRing);
+      plan.cnt_seq++;
+    }
+    double mb = 8.0 * (double)n;
+    int nk = 3;
+    for (int side = 0; side < 2; side++) {
+      if (!cp.s[side].on) continue;
+      cmap[side] = reinterpret_cast<uint32_t*>(at);
+      at += cp.s[side].map_bytes;
+      M.map[side] = cmap[side];
+      M.c[side] = cp.s[side].c;
+      M.nw[side] = (int64_t)cp.s[side].nw;
+      M.sums[side] = reinterpret_cast<uint32_t*>(at);
+      at += cp.s[side].sums_bytes;
+      M.count[side] = cnt ? cnt + side : nullptr;
+      ccount[side] = M.count[side];
+      mb += 28.0 * (double)cp.s[side].nw;  // zero, count, rank
+      nk++;
+    }
+    cfin = at;
+    void* e1 = nullptr;
+    if (prof) prof_begin(plan, 2, mb, st, &e1, nk);
+    launch_block_maps(M, st);
+    if (prof) prof_end(plan, e1, st);
+  }
+  auto cbuf = [&](size_t i, int side) -> void* {
+    return cfin + i * cp.per_final + (side && cp.s[0].on ? cp.s[0].buf_bytes : 0);
+  };
+
   // gather template
   GatherLaunch G;
   std::memset(&G, 0, sizeof(G));
@@ -353,6 +514,10 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
     const SegmentPlan& fin = side ? finB : finA;
     const HalfPlan& H = side ? plan.B : plan.A;
     GatherSide& gs = side ? G.B : G.A;
+    if (cmap[side]) {
+      gs.c = cp.s[side].c;
+      gs.c.cmap = cmap[side];
+    }
     if (fin.pins_out.size() > (size_t)MAX_PINS) fail(SF_EUNSUPPORTED, "too many pins at gather");
     gs.npin = (int)fin.pins_out.size();
     for (size_t i = 0; i < fin.pins_out.size(); i++) {
@@ -498,6 +663,13 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
       // finals
       std::vector<Job> jobsA, jobsB;
       std::vector<GatherFinal> gf;
+      CompactOut coA, coB;
+      for (int side = 0; side < 2; side++) {
+        CompactOut& co = side ? coB : coA;
+        co.cmap = cmap[side];
+        co.ctl = cp.s[side].c.ctl;
+        co.count = ccount[side];
+      }
       for (size_t i = 0; i < block.size(); i++) {
         const uint64_t fpath = block[i].fid << fb;
         const void *inA = nullptr, *inB = nullptr;
@@ -523,6 +695,14 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         std::memset(&g, 0, sizeof(g));
         g.wa = bufA(fs);
         g.wb = bufB(fs);
+        if (cmap[0]) {
+          coA.out.push_back(cbuf(i, 0));
+          g.wa = coA.out.back();
+        }
+        if (cmap[1]) {
+          coB.out.push_back(cbuf(i, 1));
+          g.wb = coB.out.back();
+        }
         g.path = fpath;
         cd sc = psa * finA.scale * psb * finB.scale;
         g.sre = sc.real();
@@ -531,8 +711,8 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         std::memcpy(g.leafmask, block[i].mask, sizeof(g.leafmask));
         gf.push_back(g);
       }
-      run_segment(*C, plan, finA, jobsA, st, prof, err);
-      run_segment(*C, plan, finB, jobsB, st, prof, err);
+      run_segment(*C, plan, finA, jobsA, st, prof, err, cmap[0] ? &coA : nullptr);
+      run_segment(*C, plan, finB, jobsB, st, prof, err, cmap[1] ? &coB : nullptr);
       if (plan.opts.exec_mode == SF_EXEC_PLAIN) {
         // the plain form shares nothing below the selection prefix: every
         // path re-evolves its levels under the prefix checkpoint

@@ -238,6 +238,24 @@ __global__ void __launch_bounds__(R >= 5 ? 320 : 576, 1) pass_kernel(const __gri
 }
 
 // ------------------------------------------------------------------ gather
+// Compact finals (CompactMap): part number of a layout index, and the slot
+// of a part (marked parts below it; every requested bitstring's parts are
+// marked).
+__device__ __forceinline__ uint32_t compact_part(const CompactMap& c, uint32_t j) {
+  return (pext32(j, c.cfree) << c.ckt) | pext32(j, c.cpart);
+}
+__device__ __forceinline__ uint32_t compact_slot(const uint32_t* cmap, uint32_t p) {
+  const uint2 w = reinterpret_cast<const uint2*>(cmap)[p >> 5];
+  return w.y + (uint32_t)__popc(w.x & ((1u << (p & 31)) - 1u));
+}
+// Index of amplitude j (layout index) of a final; h0 / h1: slot * 2^ctl of
+// the block's first / second part.
+__device__ __forceinline__ uint32_t compact_index(const CompactMap& c, uint32_t h0, uint32_t h1, uint32_t j) {
+  if (!c.cmap) return j;
+  const uint32_t h = (c.csub1 && ((j >> c.ctl) & 1u)) ? h1 : h0;
+  return h | (j & ((1u << c.ctl) - 1u));
+}
+
 template <int G>
 __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherLaunch P) {
   __shared__ uint32_t tA[8 * 256], tB[8 * 256];
@@ -265,6 +283,19 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       xa[t] = (int)((x >> P.A.dq[t]) & 1u);
       xb[t] = (int)((x >> P.B.dq[t]) & 1u);
     }
+    // compact finals: slots of the parts of the bitstring's blocks (ia, ib
+    // are zero at the block positions 0..G-1)
+    uint32_t ha0 = 0, ha1 = 0, hb0 = 0, hb1 = 0;
+    if (P.A.c.cmap) {
+      const uint32_t p0 = compact_part(P.A.c, ia);
+      ha0 = compact_slot(P.A.c.cmap, p0) << P.A.c.ctl;
+      if (P.A.c.csub1) ha1 = compact_slot(P.A.c.cmap, p0 | P.A.c.csub1) << P.A.c.ctl;
+    }
+    if (P.B.c.cmap) {
+      const uint32_t p0 = compact_part(P.B.c, ib);
+      hb0 = compact_slot(P.B.c.cmap, p0) << P.B.c.ctl;
+      if (P.B.c.csub1) hb1 = compact_slot(P.B.c.cmap, p0 | P.B.c.csub1) << P.B.c.ctl;
+    }
     double sr = 0.0, si = 0.0;
     for (int f = 0; f < P.n_finals; f++) {
       const GatherFinal& F = P.finals[f];
@@ -288,8 +319,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
           ja |= (uint32_t)((y >> t) & 1) << P.A.dpos[t];
           jb |= (uint32_t)((y >> t) & 1) << P.B.dpos[t];
         }
-        wa[y] = ((ja & pam) == pav) ? WA[ja] : make_float2(0.f, 0.f);
-        wb[y] = ((jb & pbm) == pbv) ? WB[jb] : make_float2(0.f, 0.f);
+        wa[y] = ((ja & pam) == pav) ? WA[compact_index(P.A.c, ha0, ha1, ja)] : make_float2(0.f, 0.f);
+        wb[y] = ((jb & pbm) == pbv) ? WB[compact_index(P.B.c, hb0, hb1, jb)] : make_float2(0.f, 0.f);
       }
       float2 c = make_float2(0.f, 0.f);
       if (G == 0) {
@@ -377,6 +408,103 @@ __global__ void frugal_accept_kernel(const double* amps, const double* u, int64_
   }
   for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
   if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
+}
+
+// ------------------------------------------------------ compact final maps
+// Mark, per half, the parts of every requested bitstring's block.
+__global__ void __launch_bounds__(256) block_mark_kernel(const __grid_constant__ BlockMapLaunch P) {
+  __shared__ uint32_t tab[2][8 * 256];
+  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) {
+    tab[0][i] = P.map[0] ? P.tab[0][i] : 0u;
+    tab[1][i] = P.map[1] ? P.tab[1][i] : 0u;
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t x = P.bits[i];
+    uint32_t ix0 = 0, ix1 = 0;
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+      const uint32_t byte = (uint32_t)(x >> (8 * b)) & 255u;
+      ix0 |= tab[0][b * 256 + byte];
+      ix1 |= tab[1][b * 256 + byte];
+    }
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+      if (!P.map[side]) continue;
+      const uint32_t p0 = compact_part(P.c[side], side ? ix1 : ix0);
+      atomicOr(&P.map[side][2 * (p0 >> 5)], 1u << (p0 & 31));
+      if (P.c[side].csub1) {
+        const uint32_t p1 = p0 | P.c[side].csub1;
+        atomicOr(&P.map[side][2 * (p1 >> 5)], 1u << (p1 & 31));
+      }
+    }
+  }
+}
+
+// Prefix counts of the marked parts: chunks of kRankChunk map words per
+// block of 256 threads (8 consecutive words a thread); pass 1 counts each
+// chunk, pass 2 adds the chunks before it and scans within the chunk.
+constexpr int kRankPer = 8;
+constexpr int kRankChunk = 256 * kRankPer;
+
+__device__ __forceinline__ uint32_t block_sum256(uint32_t v, uint32_t* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint32_t t = 0;
+  for (int q = 0; q < 8; q++) t += red[q];
+  return t;
+}
+
+__global__ void __launch_bounds__(256) block_count_kernel(const __grid_constant__ BlockMapLaunch P) {
+  const int side = blockIdx.y;
+  const int64_t nw = P.nw[side];
+  const int64_t w0 = (int64_t)blockIdx.x * kRankChunk;
+  if (!P.map[side] || w0 >= nw) return;  // uniform over the block
+  __shared__ uint32_t red[8];
+  uint32_t c = 0;
+#pragma unroll
+  for (int j = 0; j < kRankPer; j++) {
+    const int64_t w = w0 + (int64_t)threadIdx.x * kRankPer + j;
+    if (w < nw) c += (uint32_t)__popc(P.map[side][2 * w]);
+  }
+  c = block_sum256(c, red);
+  if (threadIdx.x == 0) P.sums[side][blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(256) block_rank_kernel(const __grid_constant__ BlockMapLaunch P) {
+  const int side = blockIdx.y;
+  const int64_t nw = P.nw[side];
+  const int64_t w0 = (int64_t)blockIdx.x * kRankChunk;
+  if (!P.map[side] || w0 >= nw) return;  // uniform over the block
+  __shared__ uint32_t red[8], wsum[8];
+  uint32_t before = 0;
+  for (int c = threadIdx.x; c < (int)blockIdx.x; c += blockDim.x) before += P.sums[side][c];
+  before = block_sum256(before, red);
+  uint32_t cnt[kRankPer], mine = 0;
+#pragma unroll
+  for (int j = 0; j < kRankPer; j++) {
+    const int64_t w = w0 + (int64_t)threadIdx.x * kRankPer + j;
+    cnt[j] = w < nw ? (uint32_t)__popc(P.map[side][2 * w]) : 0u;
+    mine += cnt[j];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = mine;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  uint32_t run = before + inc - mine;
+  for (int q = 0; q < warp; q++) run += wsum[q];
+#pragma unroll
+  for (int j = 0; j < kRankPer; j++) {
+    const int64_t w = w0 + (int64_t)threadIdx.x * kRankPer + j;
+    if (w < nw) P.map[side][2 * w + 1] = run;
+    run += cnt[j];
+  }
+  if (P.count[side] && w0 + kRankChunk >= nw && threadIdx.x == blockDim.x - 1) *P.count[side] = run;
 }
 
 __global__ void zero_kernel(double* p, int64_t n) {
@@ -475,6 +603,32 @@ void launch_gather(const GatherLaunch& L, void* stream) {
     default: fail(SF_EINVAL, "internal: too many deferred gates");
   }
   check(cudaGetLastError(), "gather_kernel launch");
+}
+
+int launch_block_maps(const BlockMapLaunch& L, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int launches = 0;
+  int64_t maxw = 0;
+  for (int side = 0; side < 2; side++)
+    if (L.map[side]) {
+      if (L.nw[side] < 1 || !L.sums[side]) fail(SF_EINVAL, "internal: block map without words");
+      launch_zero(reinterpret_cast<double*>(L.map[side]), L.nw[side], stream);
+      launches++;
+      maxw = std::max(maxw, L.nw[side]);
+    }
+  if (maxw == 0) return launches;
+  if (L.n > 0) {
+    const int64_t blocks = std::min<int64_t>((L.n + 255) / 256, (int64_t)num_sms() * 8);
+    block_mark_kernel<<<(int)blocks, 256, 0, s>>>(L);
+    check(cudaGetLastError(), "block_mark_kernel launch");
+    launches++;
+  }
+  const dim3 grid((unsigned)((maxw + kRankChunk - 1) / kRankChunk), 2);
+  block_count_kernel<<<grid, 256, 0, s>>>(L);
+  check(cudaGetLastError(), "block_count_kernel launch");
+  block_rank_kernel<<<grid, 256, 0, s>>>(L);
+  check(cudaGetLastError(), "block_rank_kernel launch");
+  return launches + 2;
 }
 
 void launch_zero(double* p, int64_t n, void* stream) {

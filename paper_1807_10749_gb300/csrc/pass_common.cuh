@@ -148,6 +148,7 @@ struct ItemGeo {
   uint32_t base;                 // global index bits of the tile (inactive bits)
   uint32_t lin_m, lin_v;         // input pins on tile-local bits
   uint32_t lout_m, lout_v;       // output pins on tile-local bits
+  uint32_t tile;                 // tile number (the free positions of base, packed)
   int node;
   uint64_t path;
 };
@@ -160,6 +161,7 @@ __device__ __forceinline__ ItemGeo item_geo(const PassLaunch& P, int64_t item, i
   // DRAM once and from L2 after that
   g.node = (int)(item % P.n_nodes);
   const uint32_t t = (uint32_t)(item / P.n_nodes);
+  g.tile = t;
   g.path = P.nodes[g.node].path;
   uint32_t base = 0;
   for (int i = 0; i < d.n_free; i++) base |= ((t >> i) & 1u) << d.freepos[i];
@@ -281,6 +283,60 @@ struct GenericCopy {
   }
 };
 
+// Compact store of a final pass (PassLaunch::cmap set): the tile's parts
+// (2^ctl consecutive elements each, the tile's share of one block of the
+// gather) are consecutive bits of the part map; a lane takes 32 of them per
+// round, one 8-byte load of (map word, prefix count), and writes each
+// requested part to its slot as 16-byte chunks. The store warp loads the
+// first round's words as soon as the tile's geometry is published, while the
+// compute warps work on the tile.
+struct CompactWord {
+  uint32_t bits;  // requested parts among the lane's 32 (bit j: part ub + j)
+  uint32_t rank;  // requested parts of the half below part ub
+};
+
+__device__ __forceinline__ CompactWord compact_word(const PassLaunch& P, const ItemGeo& g, int lane, int r) {
+  const int kt = P.pass.k - P.ctl;
+  const uint32_t nparts = 1u << kt;
+  const uint32_t ub = 32u * (uint32_t)(lane + 32 * r);
+  CompactWord cw{0u, 0u};
+  if (ub >= nparts) return cw;
+  const uint64_t pb = ((uint64_t)g.tile << kt) + ub;  // part number of part ub
+  const uint2 w = reinterpret_cast<const uint2*>(P.cmap)[pb >> 5];
+  const uint32_t off = (uint32_t)pb & 31u;  // nonzero only for tiles of < 32 parts
+  const uint32_t cnt = nparts - ub < 32u ? nparts - ub : 32u;
+  cw.bits = (w.x >> off) & (cnt == 32u ? 0xffffffffu : ((1u << cnt) - 1u));
+  cw.rank = w.y + (uint32_t)__popc(w.x & ((1u << off) - 1u));
+  return cw;
+}
+
+__device__ __forceinline__ void compact_write(const PassLaunch& P, const ItemGeo& g, const float2* buf, int lane,
+                                              int r, const CompactWord& cw) {
+  float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
+  const float4* srcb = reinterpret_cast<const float4*>(buf);
+  const int tl = P.ctl;
+  const int nq = 1 << (tl - 1);  // 16-byte chunks per part
+  const uint32_t ub = 32u * (uint32_t)(lane + 32 * r);
+  uint32_t bits = cw.bits;
+  while (bits) {
+    const uint32_t j = (uint32_t)__ffs(bits) - 1u;
+    bits &= bits - 1u;
+    const uint32_t slot = cw.rank + (uint32_t)__popc(cw.bits & ((1u << j) - 1u));
+    float4* dst = reinterpret_cast<float4*>(out + ((uint64_t)slot << tl));
+    const uint32_t c0 = (ub + j) << (tl - 1);
+    for (int q = 0; q < nq; q++) dst[q] = srcb[swz(2u * (c0 + (uint32_t)q)) >> 1];
+  }
+}
+
+// cw: the lane's words of round 0 (compact_word(P, g, lane, 0)).
+__device__ __forceinline__ void compact_store_tile(const PassLaunch& P, const ItemGeo& g, const float2* buf,
+                                                   int lane, const CompactWord& cw) {
+  const int kt = P.pass.k - P.ctl;
+  const int rounds = kt > 10 ? 1 << (kt - 10) : 1;
+  compact_write(P, g, buf, lane, 0, cw);
+  for (int r = 1; r < rounds; r++) compact_write(P, g, buf, lane, r, compact_word(P, g, lane, r));
+}
+
 // Prog::run(P, sm, g, w8, ncomp, active) runs the register stages of one
 // tile: every compute thread calls it and passes each stage barrier at the
 // same instruction; only active threads (below 2^(k-R)) do stage work.
@@ -366,7 +422,17 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
     int i = 0;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
       const int b = i % NBUF;
-      if (!mbar_wait(smem_u32(&empty[b]), (uint32_t)((i / NBUF) & 1)) || *(volatile int*)&abort_flag) {
+      const uint32_t par = (uint32_t)((i / NBUF) & 1);
+      // compact output: the geometry is readable once full[b] completes
+      // (buffer b cannot be refilled before this warp frees it), so load
+      // the tile's part-map words while the tile is being computed
+      CompactWord cw{0u, 0u};
+      bool ok = true;
+      if (P.cmap) {
+        ok = mbar_wait(smem_u32(&full[b]), par);
+        if (ok) cw = compact_word(P, geo[b], lane, 0);
+      }
+      if (!ok || !mbar_wait(smem_u32(&empty[b]), par) || *(volatile int*)&abort_flag) {
         if (lane == 0) {
           abort_flag = 1;
           atomicExch(P.err, 1);
@@ -374,7 +440,8 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         break;
       }
       const ItemGeo g = geo[b];
-      Prog::store_tile(P, g, bufs + b * ntile, lane, cc);
+      if (P.cmap) compact_store_tile(P, g, bufs + b * ntile, lane, cw);
+      else Prog::store_tile(P, g, bufs + b * ntile, lane, cc);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&freeb[b]));
     }

@@ -62,7 +62,20 @@ struct GatherFinal {
   uint64_t leafmask[4];       // else: selected leaf digits (bit b = leaf b)
 };
 
+// Compact finals (PassLaunch::cmap): amplitude j of a final sits at
+// slot(P) * 2^ctl + (j mod 2^ctl), P = (pext(j, cfree) << ckt) | pext(j, cpart)
+// its part; a block of the gather spans one part, or two when csub1 != 0
+// (position ctl is then a block bit; csub1 is its contribution to P).
+struct CompactMap {
+  const uint32_t* cmap;  // null: dense
+  uint32_t cfree;        // free positions of the final pass
+  uint32_t cpart;        // its active positions from ctl up
+  int32_t ckt, ctl;      // k - ctl, ctl
+  uint32_t csub1;
+};
+
 struct GatherSide {
+  CompactMap c;
   int32_t npin;
   DevPin pin[MAX_PINS];
   int8_t dpos[MAX_DEFER];  // layout positions of the deferred qubits
@@ -164,14 +177,23 @@ struct ProfRec {
   void* e0;  // cudaEvent_t
   void* e1;
 };
+// Bytes known on the device only (the compact final writes: requested blocks
+// x bytes per block), read back when the profile is collected.
+struct ProfUnits {
+  int kind;
+  const uint32_t* count;  // device counter
+  double unit;            // bytes per count
+};
 struct Profile {
   bool timing = false;
   int64_t launches[3] = {0, 0, 0};
   double bytes[3] = {0, 0, 0};
   double seconds[3] = {0, 0, 0};
   std::vector<ProfRec> pending;
+  std::vector<ProfUnits> units;
   std::vector<void*> pool;
 };
+constexpr int kCountRing = 1024;  // calls whose block counts the profile can hold
 
 struct Plan {
   sf_plan_opts opts;
@@ -193,6 +215,8 @@ struct Plan {
   uint32_t* d_tabA = nullptr;
   uint32_t* d_tabB = nullptr;
   int* d_err = nullptr;  // device error flag of bounded waits
+  uint32_t* d_cnt = nullptr;  // requested-block counts per call and half (kCountRing x 2)
+  uint64_t cnt_seq = 0;
   int device = 0;
   // executor cache (resident nodes between calls that reuse a workspace)
   void* cache = nullptr;
@@ -242,7 +266,7 @@ void launch_pass_jit(const PassLaunch& L, int tiles, void* entry, void* stream);
 void ensure_device(Plan& p);
 void exec_release_cache(Plan& p);
 double segment_bytes(const SegmentPlan& s);  // algorithmic bytes of one node
-void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out);
+void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out, int launches = 1);
 void prof_end(Plan& p, void* e1, void* stream);
 void prof_collect(Plan& p);
 void prof_release(Plan& p);
@@ -250,6 +274,22 @@ void prof_release(Plan& p);
 // ---------------------------------------------------------------- kernels
 void launch_pass(const PassLaunch& L, int tiles, int fuse_bits, int tile_bits, void* stream);
 void launch_gather(const GatherLaunch& L, void* stream);
+// Part maps of the compact finals (PassLaunch::cmap) for n bitstrings: per
+// half with map != null, zero the map, mark the parts of every bitstring's
+// block, then fill the per-word prefix counts (sums: scratch of
+// ceil(nw / 2048) words) and write the number of marked parts to count
+// (unless null).
+struct BlockMapLaunch {
+  const uint32_t* tab[2];
+  const uint64_t* bits;
+  int64_t n;
+  CompactMap c[2];   // c[s].cmap unused here: map[s] is written
+  uint32_t* map[2];
+  int64_t nw[2];
+  uint32_t* sums[2];
+  uint32_t* count[2];
+};
+int launch_block_maps(const BlockMapLaunch& L, void* stream);  // returns kernels launched
 void launch_zero(double* p, int64_t n_doubles, void* stream);
 void launch_overlap(const double* a, const double* b, int64_t n, double* out, void* stream);
 void launch_frugal(const double* amps, const double* u, int64_t n, double N, double mp, double scale,

@@ -51,7 +51,7 @@ class sf_plan_opts(ctypes.Structure):
                 ("defer_last_level", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("batch_paths", ctypes.c_int32), ("run_bits", ctypes.c_int32),
                 ("jit", ctypes.c_int32), ("split_last", ctypes.c_int32), ("fp32x2", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("dense_finals", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class sf_path_sel(ctypes.Structure):
