@@ -221,7 +221,10 @@ SF_API int sf_selection_ids(const sf_plan* p, const sf_path_sel* sel, uint64_t* 
 SF_API int sf_amplitudes(sf_plan* p, const uint64_t* bitstrings, int64_t n, const sf_path_sel* sel,
                   double* out_amps, double* out_f_actual);
 
-/* Device form: bytes of device workspace sf_amplitudes_device needs. */
+/* Device form: bytes of device workspace sf_amplitudes_device needs for n
+ * bitstrings and this selection: the path-tree node buffers and, when the
+ * plan writes compact finals (sf_plan_opts.dense_finals), the part maps and
+ * compact buffers, which grow with n. */
 SF_API int sf_workspace_size(const sf_plan* p, int64_t n, const sf_path_sel* sel, size_t* bytes);
 
 /* Device form: d_bitstrings (n uint64) and d_out_amps (2n doubles) are device
@@ -310,7 +313,9 @@ SF_API void sf_server_destroy(sf_server* s);
  * or 2 (other), the launches since the reset, their summed device time in
  * seconds (0 unless timing was on; blocks until those launches finished)
  * and their algorithmic bytes (state amplitudes read + written, 8 bytes each,
- * for passes; bitstrings, gathered amplitudes and accumulators for gathers). */
+ * for passes, where a compact final pass counts the parts it writes;
+ * bitstrings, gathered amplitudes and accumulators for gathers). Reading
+ * waits for the device when compact final passes were counted. */
 SF_API int sf_plan_profile(sf_plan* p, int enable_timing);
 SF_API int sf_plan_profile_read(sf_plan* p, int kernel, int64_t* launches, double* seconds, double* bytes);
 
