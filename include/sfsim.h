@@ -224,7 +224,8 @@ SF_API int sf_amplitudes(sf_plan* p, const uint64_t* bitstrings, int64_t n, cons
 /* Device form: bytes of device workspace sf_amplitudes_device needs for n
  * bitstrings and this selection: the path-tree node buffers and, when the
  * plan writes compact finals (sf_plan_opts.dense_finals), the part maps and
- * compact buffers, which grow with n. */
+ * compact buffers, which grow with n. Needs no device when the plan was
+ * made with hbm_budget_bytes > 0. */
 SF_API int sf_workspace_size(const sf_plan* p, int64_t n, const sf_path_sel* sel, size_t* bytes);
 
 /* Device form: d_bitstrings (n uint64) and d_out_amps (2n doubles) are device

@@ -322,7 +322,8 @@ int sf_workspace_size(const sf_plan* h, int64_t n, const sf_path_sel* sel, size_
   SF_GUARD_BEGIN
   if (!h || !sel || !bytes) sf::fail(SF_EINVAL, "null argument");
   if (n < 0) sf::fail(SF_EINVAL, "negative bitstring count");
-  ensure_device(*const_cast<sf::Plan*>(h->p));
+  // the size depends on the device only through the default memory budget
+  if (h->p->opts.hbm_budget_bytes == 0) ensure_device(*const_cast<sf::Plan*>(h->p));
   *bytes = sf::exec_workspace_bytes(*h->p, n, *sel);
   return SF_OK;
   SF_GUARD_END
