@@ -7,7 +7,8 @@ bitmap word and the count of marked parts before it) is built here, in
 Python, from random requested indices. Every amplitude of a requested block
 must then be found where the gather looks for it, slot(part) * 2^ctl + its
 offset in the part; nothing else may be written, and no write may leave the
-buffer."""
+buffer. The gather's own index functions, compiled in too, must read every
+requested amplitude's value back."""
 import os
 import random
 import shutil
@@ -36,6 +37,17 @@ inline int __ffs(unsigned v) { return __builtin_ffs((int)v); }
 '''
 
 
+def _gather_index_code():
+    """The gather's compact-final index functions and their record."""
+    h = open(os.path.join(CSRC, "sf_internal.h")).read()
+    k = open(os.path.join(CSRC, "kernels.cu")).read()
+    a = h.index("struct CompactMap {")
+    b = h.index("struct GatherSide {")
+    c = k.index("__device__ __forceinline__ uint32_t compact_part(")
+    d = k.index("template <int G>", c)
+    return h[a:b] + k[c:d]
+
+
 def _extract():
     src = open(os.path.join(CSRC, "pass_common.cuh")).read()
     a = src.index("struct ItemGeo {")
@@ -44,7 +56,7 @@ def _extract():
     d = src.index("};", c) + 2
     e = src.index("struct CompactWord {")
     f = src.index("\n}\n", src.index("__device__ __forceinline__ void compact_store_tile(")) + 3
-    return src[a:b] + "\n" + src[c:d] + "\n" + src[e:f]
+    return src[a:b] + "\n" + src[c:d] + "\n" + src[e:f] + "\n" + _gather_index_code()
 
 
 DRIVER = r'''
@@ -101,6 +113,28 @@ int main() {
     }
   }
   for (long i = 0; i < (long)out.size(); i++) printf("%.1f %.1f\n", out[i].x, out[i].y);
+  // the gather's reads: every amplitude of each requested block, through its
+  // index functions (stdin: cfree cpart csub1 nreq req[nreq])
+  CompactMap cm;
+  std::memset(&cm, 0, sizeof(cm));
+  cm.cmap = map.data();
+  cm.ckt = k - tl;
+  cm.ctl = tl;
+  long nreq;
+  if (scanf("%u %u %u %ld", &cm.cfree, &cm.cpart, &cm.csub1, &nreq) != 4) return 3;
+  const float2* fin = out.data() + guard;
+  for (long r = 0; r < nreq; r++) {
+    uint32_t gi;
+    scanf("%u", &gi);
+    const uint32_t base = gi & ~((1u << g) - 1u);
+    const uint32_t p0 = compact_part(cm, base);
+    const uint32_t h0 = compact_slot(cm.cmap, p0) << cm.ctl;
+    const uint32_t h1 = cm.csub1 ? compact_slot(cm.cmap, p0 | cm.csub1) << cm.ctl : 0u;
+    for (uint32_t o = 0; o < (1u << g); o++) {
+      const float2 v = fin[compact_index(cm, h0, h1, base | o)];
+      printf("G %u %.1f\n", base | o, v.x);
+    }
+  }
   return 0;
 }
 '''
@@ -172,9 +206,17 @@ def test_compact_store_writes_exactly_the_requested_parts(harness, m, k, L, g, e
     inp = [m, k, L, g, *gpos, len(free), *free, len(words)]
     inp += [v for w, r in zip(words, ranks) for v in (w, r)]
     inp.append(cap)
+    kt = k - tl
+    csub1 = (_pext(1 << tl, free) << kt) if g > tl else 0
+    inp += [sum(1 << p for p in free), sum(1 << p for p in gpos[tl:]), csub1, len(requested), *requested]
     out = subprocess.run([harness], input=" ".join(map(str, inp)), capture_output=True, text=True, timeout=120)
     assert out.returncode == 0, out.stderr
-    vals = [tuple(map(float, ln.split())) for ln in out.stdout.split("\n") if ln.strip()]
+    lines = [ln for ln in out.stdout.split("\n") if ln.strip()]
+    greads = [ln.split()[1:] for ln in lines if ln.startswith("G ")]
+    assert len(greads) == len(requested) << g
+    for idx, v in greads:
+        assert float(idx) == float(v), (idx, v)   # the gather finds each amplitude's own value
+    vals = [tuple(map(float, ln.split())) for ln in lines if not ln.startswith("G ")]
     guard = 64
     assert len(vals) == (cap << tl) + 2 * guard
     assert all(v == (-7.0, -7.0) for v in vals[:guard] + vals[-guard:]), "write outside the buffer"
