@@ -173,6 +173,17 @@ def cpu_baseline_sample(text, mask, bits_all):
             "seconds": dt}
 
 
+def amplitude_rates(paths_per_s, n_bits, n_selected):
+    """Amplitude throughput beside paths/s: path-amplitude contributions per
+    second (every path adds one term to each requested amplitude), and
+    finished amplitudes per second of the whole request, extrapolated from
+    the timed prefixes to all n_selected paths at the same rate."""
+    return {"path_amplitudes_per_s": paths_per_s * n_bits,
+            "request_amplitudes_per_s": n_bits * paths_per_s / n_selected,
+            "request_seconds": n_selected / paths_per_s,
+            "note": "request figures extrapolated from the timed 128-path prefixes to the whole selection"}
+
+
 def rank_prefixes(first_ids, world, rank, n_steps):
     """First path id of each 128-path prefix this rank processes: every
     world-th prefix of the sorted selection (the ranks' sets are disjoint)."""
@@ -480,6 +491,7 @@ def main():
                         "gather": {"launches": gat_n, "seconds": gat_s, "bytes": gat_b},
                         "other": {"launches": oth_n}},
             "gpu_launches": pass_n + gat_n + oth_n,
+            "amplitudes": amplitude_rates(value, len(bits), n_sel),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * len(bits),
                     "d2h_bytes_per_step": 16 * len(bits), "steps": e2e_steps,
                     "host_buffers": "pinned (sf_amplitudes with host pointers)"},

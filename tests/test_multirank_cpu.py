@@ -51,3 +51,11 @@ def test_single_rank_is_identity():
     ids = np.arange(128 * 3, dtype=np.uint64)
     assert bench.rank_prefixes(ids, 1, 0, 3) == [0, 128, 256]
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_amplitude_rates():
+    import bench
+    r = bench.amplitude_rates(3000.0, 1_000_000, 171_798_912)
+    assert r["path_amplitudes_per_s"] == 3e9
+    assert abs(r["request_seconds"] - 171_798_912 / 3000.0) < 1e-6
+    assert abs(r["request_amplitudes_per_s"] * r["request_seconds"] - 1_000_000) < 1e-3
