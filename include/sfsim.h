@@ -109,17 +109,19 @@ typedef struct {
                                 index bits every pass keeps active), 0 = per
                                 segment the width (4 or 3) whose program moves
                                 fewer bytes */
-  int32_t jit;              /* 1 = compile every pass of the plan into a kernel of
-                               its own at plan time (NVRTC; SF_EUNSUPPORTED where
-                               NVRTC is missing), 0 = the generic pass kernel */
+  int32_t jit;              /* 1 (default) = compile every pass of the plan into a
+                               kernel of its own at plan time (NVRTC; plan creation
+                               fails with SF_EUNSUPPORTED where NVRTC is missing),
+                               0 = the generic pass kernel */
   int32_t split_last;       /* with the last level folded into the gather: 0 = plan
                                the level before it and the last segment as one
                                program (no node is written between them), 1 = two
                                programs with the node in between */
   int32_t fp32x2;           /* specialised kernels: 1 = register stages made only of
-                               H, X^1/2, Y^1/2 and phase groups hold amplitude
-                               pairs in FP32x2 registers (packed adds), 0 = scalar
-                               (default; measured 3% faster on the 7x8 workload) */
+                               H, X^1/2, Y^1/2 and phase groups keep each complex
+                               amplitude in one FP32x2 register pair, so a
+                               butterfly is one packed add per output; 0 = scalar
+                               FP32 arithmetic */
   int32_t dense_finals;     /* with the last level folded into the gather: 0 = the
                                last pass of each half's final program writes only
                                the blocks of 2^g amplitudes (g = cut gates of the
@@ -127,14 +129,32 @@ typedef struct {
                                a compact buffer, when that is at most a quarter of
                                the half and fits the budget; 1 = always write the
                                whole final state */
-  int32_t reserved[2];
+  int32_t precision;        /* SF_PREC_*: how the cross-path sum accumulates */
+  int32_t reserved;
 } sf_plan_opts;
+
+/* Precision of the path sum (Section 2 footnote: single-precision states,
+ * higher-precision accumulators). The half states are complex64 and each
+ * path's product A_j[x_A] * B_j[x_B] is formed in FP32 in every mode.
+ *   SF_PREC_F64: the products are added to FP64 sums, one final after another
+ *     in path order, starting from the output (the default).
+ *   SF_PREC_COMPENSATED: the same FP64 additions with Neumaier compensation;
+ *     the compensation terms (16 bytes per bitstring of workspace) are added
+ *     to the output at the end of the call.
+ * In both modes the order of additions is fixed by the path order alone, so
+ * a result does not depend on the memory budget, the batch size or the
+ * requests it was batched with. */
+enum { SF_PREC_F64 = 0, SF_PREC_COMPENSATED = 1 };
 
 SF_API void sf_plan_opts_default(sf_plan_opts* o);
 
 /* Plan the simulation: cut, cross gates (time order (cycle, lower qubit,
- * higher qubit)), decomposition, path tree, fused passes. Uses the current
- * CUDA device (uploads the pass programs). */
+ * higher qubit)), decomposition, path tree, fused passes. When a CUDA device
+ * is present, the plan's device state is set up on the current device here
+ * (gather tables, the wait-timeout flag, the memory budget) and every kernel
+ * the plan runs is loaded, so that later calls load no code. Without a device
+ * the plan can still be inspected and sized (sf_plan_info, sf_workspace_size
+ * with a budget, sf_selection_*). */
 SF_API int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out);
 
 /* n_cross: cross gates; path_bits: log2 of the path count (each cross gate
@@ -232,10 +252,59 @@ SF_API int sf_workspace_size(const sf_plan* p, int64_t n, const sf_path_sel* sel
  * pointers; d_workspace of ws_bytes >= sf_workspace_size(). All work is
  * enqueued on cuda_stream; the call returns after the last launch is enqueued
  * and the result is valid once the stream reaches it. With accumulate != 0 the
- * sums are added to d_out_amps; otherwise d_out_amps is overwritten. */
+ * sums are added to d_out_amps; otherwise d_out_amps is overwritten. Check
+ * sf_plan_status once the stream is done: a kernel whose bounded wait gave
+ * up leaves the result invalid. */
 SF_API int sf_amplitudes_device(sf_plan* p, const uint64_t* d_bitstrings, int64_t n, const sf_path_sel* sel,
                          double* d_out_amps, int accumulate, void* d_workspace, size_t ws_bytes,
                          void* cuda_stream);
+
+/* Several requests on one plan at once (Section 2: paths are independent, so
+ * requests that share a circuit share its path tree). The union of the
+ * requests' selected paths is evolved once: every pass launch carries the
+ * nodes of all requests, and each request's bitstrings are gathered from the
+ * finals it selected into its own output. Each request's result is bit for
+ * bit the one sf_amplitudes_device gives it alone. All pointers in reqs are
+ * device pointers (sel is host memory, read during the call). */
+typedef struct {
+  const uint64_t* d_bitstrings;  /* n uint64 */
+  int64_t n;
+  const sf_path_sel* sel;
+  double* d_out_amps;            /* 2n doubles */
+  int32_t accumulate;
+} sf_request;
+SF_API int sf_workspace_size_batch(const sf_plan* p, const sf_request* reqs, int n_req, size_t* bytes);
+SF_API int sf_amplitudes_device_batch(sf_plan* p, const sf_request* reqs, int n_req, void* d_workspace,
+                                      size_t ws_bytes, void* cuda_stream);
+
+/* Status of the device forms: waits for cuda_stream, then reads and clears
+ * the plan's wait-timeout flag. Every wait inside the pass kernels is bounded
+ * (about 2^31 cycles); one that gives up sets this flag and ends its kernel,
+ * which leaves the amplitudes of that call invalid. Returns SF_ECUDA if the
+ * flag was set (or a timeout was injected, below), SF_OK otherwise. The host
+ * forms (sf_amplitudes, sf_probabilities) and the server check the flag
+ * themselves and return SF_ECUDA for the call or request concerned. */
+SF_API int sf_plan_status(sf_plan* p, void* cuda_stream);
+
+/* Test hook (host side, nothing is run on the device): the next `count`
+ * checks of a wait-timeout flag, in any form, report a timeout as if a
+ * kernel had set the flag. count = 0 cancels pending injections. */
+SF_API int sf_debug_inject_wait_timeouts(int count);
+/* Test hook: writes `value` into the plan's device wait-timeout flag (as a
+ * kernel that gave up would write 1), so the flag-reading path of every form
+ * can be tested without a timeout on the device. Synchronous. */
+SF_API int sf_debug_set_wait_flag(sf_plan* p, int value);
+
+/* Probabilities (Section 3; Section 4 samples from them): p_i = |amp_i|^2,
+ * divided by f_actual when divide_by_f != 0 (f_actual = selected paths /
+ * all paths, the fidelity of a truncated path sum). Host form: as
+ * sf_amplitudes, writing n doubles. Device form: probabilities of 2n-double
+ * amplitudes d_amps into n doubles d_probs, times `scale`, computed in FP64
+ * as (re*re + im*im) * scale in that order without contraction. */
+SF_API int sf_probabilities(sf_plan* p, const uint64_t* bitstrings, int64_t n, const sf_path_sel* sel,
+                            int divide_by_f, double* out_probs, double* out_f_actual);
+SF_API int sf_probabilities_device(const double* d_amps, int64_t n, double scale, double* d_probs,
+                                   void* cuda_stream);
 
 /* Frugal rejection sampling, the accept step of Algorithm 2 (Section 4):
  * candidate j (a uniformly drawn bitstring whose amplitude is d_amps[2j],
@@ -253,30 +322,39 @@ SF_API int sf_frugal_accept_device(const double* d_amps, const double* d_uniform
 
 /* Fidelity estimate between two sets of amplitudes on the same bitstrings
  * (Appendix C, the validation protocol; Section 3): with a = d_amps_a and
- * b = d_amps_b (2n doubles each, interleaved), writes to d_out (4 doubles,
- * device) Re and Im of sum_j conj(a_j) b_j, sum_j |a_j|^2 and sum_j |b_j|^2,
- * accumulated in FP64. The estimate is f_e = |<a|b>|^2 / (<a|a> <b|b>).
- * Enqueued on cuda_stream. */
+ * b = d_amps_b (2n doubles each, interleaved), writes to d_out (5 doubles,
+ * device) Re and Im of sum_j conj(a_j) b_j, sum_j |a_j|^2, sum_j |b_j|^2,
+ * accumulated in FP64, and the estimate f_e = |<a|b>|^2 / (<a|a> <b|b>)
+ * (0 when a norm is zero). Enqueued on cuda_stream. */
 SF_API int sf_overlap_device(const double* d_amps_a, const double* d_amps_b, int64_t n, double* d_out,
                              void* cuda_stream);
 
 /* Fixed-scratch form of sf_amplitudes_device. This call has no counterpart
- * in the paper; it exists for callers that must not allocate device memory
- * once they run (cudaMalloc may synchronise the device, and fails when
- * another allocator in the process already holds the free memory). All of its
- * scratch - the path-tree node buffers, the gather tables and the wait error
- * flag - lives in one array of SF_NOALLOC_SCRATCH_BYTES compiled into the
- * library, which every GPU that loads the library keeps until process exit.
- * Arguments are those of sf_amplitudes_device minus the workspace: d_bitstrings
- * (n uint64) and d_out_amps (2n doubles, overwritten unless accumulate != 0)
- * are caller-owned device buffers; the work is enqueued on cuda_stream.
- * The call never calls cudaMalloc or cudaFree. Its first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. A plan whose one
- * path needs more node memory than the array holds is rejected with SF_ENOMEM
- * and a message. All calls share the one array, which keeps the previous
- * call's contents; calls that can overlap on the GPU (other streams, other
- * threads) race on it and must be serialised by the caller. */
+ * in the paper. It serves callers that must not allocate device memory once
+ * they run: cudaMalloc may synchronise the device, and fails when another
+ * allocator in the process (a framework's caching allocator, say) already
+ * holds the free memory. The workspace that sf_amplitudes_device takes from
+ * its caller - path-tree node buffers, compact-final maps and buffers, and
+ * the compensation terms of SF_PREC_COMPENSATED - lives instead in one array
+ * of SF_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library's module keeps until process exit. Arguments are those of
+ * sf_amplitudes_device minus the workspace: d_bitstrings (n uint64) and
+ * d_out_amps (2n doubles, overwritten unless accumulate != 0) are caller-owned
+ * device buffers; the work is enqueued on cuda_stream.
+ *   - The call never calls cudaMalloc, cudaFree or an allocating library
+ *     routine, and loads no code: the plan must have been created with this
+ *     device current (sf_plan_create then allocates the plan's gather tables
+ *     and wait-timeout flag, loads every kernel the plan runs and looks up the
+ *     array's device address with cudaGetSymbolAddress). Otherwise SF_EINVAL.
+ *   - A plan and request whose workspace would exceed the array are rejected
+ *     with SF_ENOMEM and a message naming the bytes needed.
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents (every byte a call reads it has written first, and the
+ *     compensation terms are zeroed per call); calls that can overlap on the
+ *     GPU (other streams, other threads) race on it and must be serialised by
+ *     the caller.
+ *   - Results equal sf_amplitudes_device's bit for bit. A wait timeout is
+ *     reported by sf_plan_status, as for the device form. */
 #define SF_NOALLOC_SCRATCH_BYTES (64ull << 20)
 SF_API int sf_amplitudes_device_noalloc(sf_plan* p, const uint64_t* d_bitstrings, int64_t n,
                                         const sf_path_sel* sel, double* d_out_amps, int accumulate,
@@ -306,6 +384,9 @@ SF_API int sf_server_times(sf_server* s, uint64_t ticket, double* queued_s, doub
  * arrival order) and, if it does not fit, blocks admission until memory
  * frees. coeffs = NULL restores arrival order. */
 SF_API int sf_server_set_cost_model(sf_server* s, const double* coeffs, double max_wait_s);
+/* Batches the server has run and the requests in them (a batch holds the
+ * queued requests of one plan, run together). Any pointer may be NULL. */
+SF_API int sf_server_stats(sf_server* s, int64_t* batches, int64_t* requests, int64_t* max_batch);
 SF_API void sf_server_destroy(sf_server* s);
 
 /* Kernel counters of one plan, for roofline reports. sf_plan_profile resets

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -48,9 +49,28 @@ static void cuda_check(cudaError_t e, const char* what) {
                                  std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// Device-side state of a plan, created on first use (plan creation itself
-// makes no CUDA call): the gather byte tables and the memory budget.
+// Device-side state of a plan: the gather byte tables, the wait-timeout
+// flag, the profile's count ring and the memory budget; every kernel the plan
+// runs is loaded into the device's context here as well. Set up when the plan
+// is created if a device is present, else on first use.
 namespace sf {
+
+static std::atomic<int> g_inject_timeouts{0};
+
+void check_wait_flag(int* d_flag, void* stream) {
+  cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+  int flag = 0;
+  if (d_flag) cuda_check(cudaMemcpy(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
+  if (flag) {
+    cuda_check(cudaMemset(d_flag, 0, sizeof(int)), "cudaMemset");
+    fail(SF_ECUDA, "a kernel wait timed out (error flag set); the results of that call are invalid");
+  }
+  int v = g_inject_timeouts.load();
+  while (v > 0 && !g_inject_timeouts.compare_exchange_weak(v, v - 1)) {
+  }
+  if (v > 0) fail(SF_ECUDA, "a kernel wait timed out (injected); the results of that call are invalid");
+}
+
 void ensure_device(sf::Plan& p) {
   if (p.d_tabA) return;
   cuda_check(cudaGetDevice(&p.device), "cudaGetDevice");
@@ -80,6 +100,18 @@ void ensure_device(sf::Plan& p) {
   p.d_cnt = cnt;
   p.d_tabA = a;
   p.d_tabB = b;
+  preload_kernels();
+  if (p.opts.jit) jit_load(p);
+  noalloc_prepare(p.device);
+}
+
+static bool have_device() {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
 }
 }  // namespace sf
 using sf::ensure_device;
@@ -133,6 +165,8 @@ void sf_plan_opts_default(sf_plan_opts* o) {
   o->select_prefix_bits = -1;
   o->exec_mode = SF_EXEC_BATCHED;
   o->defer_last_level = 1;
+  o->jit = 1;
+  o->precision = SF_PREC_F64;
 }
 
 int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out) {
@@ -155,17 +189,17 @@ int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out)
   }
   if (o.jit != 0 && o.jit != 1) sf::fail(SF_EINVAL, "jit must be 0 or 1");
   if (o.dense_finals != 0 && o.dense_finals != 1) sf::fail(SF_EINVAL, "dense_finals must be 0 or 1");
+  if (o.precision != SF_PREC_F64 && o.precision != SF_PREC_COMPENSATED) sf::fail(SF_EINVAL, "unknown precision");
   sf::Plan* p = sf::plan_create(c->c, o);
-  if (o.jit) {
-    try {
-      sf::jit_prepare(*p);
-    } catch (...) {
-      sf::plan_destroy(p);
-      throw;
-    }
-  }
   sf_plan* h = new sf_plan();
   h->p = p;
+  try {
+    if (o.jit) sf::jit_prepare(*p);
+    if (sf::have_device()) ensure_device(*p);
+  } catch (...) {
+    sf_plan_destroy(h);
+    throw;
+  }
   *out = h;
   return SF_OK;
   SF_GUARD_END
@@ -341,6 +375,79 @@ int sf_amplitudes_device(sf_plan* h, const uint64_t* d_bits, int64_t n, const sf
   SF_GUARD_END
 }
 
+static std::vector<sf::ExecReq> batch_reqs(const sf::Plan& p, const sf_request* reqs, int n_req) {
+  if (n_req < 0 || (n_req > 0 && !reqs)) sf::fail(SF_EINVAL, "bad request array");
+  std::vector<sf::ExecReq> v(n_req);
+  for (int i = 0; i < n_req; i++) {
+    const sf_request& r = reqs[i];
+    if (!r.sel) sf::fail(SF_EINVAL, "request without a selection");
+    if (r.n < 0) sf::fail(SF_EINVAL, "negative bitstring count");
+    if (r.n > 0 && (!r.d_bitstrings || !r.d_out_amps)) sf::fail(SF_EINVAL, "null device buffer");
+    double fa = 0;
+    v[i].rs = sf::select_ranges(p, *r.sel, &fa);
+    v[i].d_bits = r.d_bitstrings;
+    v[i].n = r.n;
+    v[i].d_out = r.d_out_amps;
+    v[i].accumulate = r.accumulate;
+  }
+  return v;
+}
+
+int sf_workspace_size_batch(const sf_plan* h, const sf_request* reqs, int n_req, size_t* bytes) {
+  SF_GUARD_BEGIN
+  if (!h || !bytes) sf::fail(SF_EINVAL, "null argument");
+  if (h->p->opts.hbm_budget_bytes == 0) ensure_device(*const_cast<sf::Plan*>(h->p));
+  auto v = batch_reqs(*h->p, reqs, n_req);
+  *bytes = sf::exec_workspace_bytes(*h->p, v);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_amplitudes_device_batch(sf_plan* h, const sf_request* reqs, int n_req, void* d_ws, size_t ws_bytes,
+                               void* stream) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  ensure_device(*h->p);
+  auto v = batch_reqs(*h->p, reqs, n_req);
+  sf::exec_run(*h->p, v, d_ws, ws_bytes, stream, true);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_plan_status(sf_plan* h, void* stream) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  sf::check_wait_flag(h->p->d_err, stream);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_debug_inject_wait_timeouts(int count) {
+  SF_GUARD_BEGIN
+  if (count < 0) sf::fail(SF_EINVAL, "negative count");
+  sf::g_inject_timeouts.store(count);
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_debug_set_wait_flag(sf_plan* h, int value) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  ensure_device(*h->p);
+  cuda_check(cudaMemcpy(h->p->d_err, &value, sizeof(int), cudaMemcpyHostToDevice), "cudaMemcpy");
+  return SF_OK;
+  SF_GUARD_END
+}
+
+int sf_probabilities_device(const double* d_amps, int64_t n, double scale, double* d_probs, void* stream) {
+  SF_GUARD_BEGIN
+  if (n < 0 || (n > 0 && (!d_amps || !d_probs))) sf::fail(SF_EINVAL, "bad argument");
+  if (!(scale >= 0)) sf::fail(SF_EINVAL, "the scale must be >= 0");
+  sf::launch_prob(d_amps, n, scale, d_probs, stream);
+  return SF_OK;
+  SF_GUARD_END
+}
+
 int sf_frugal_accept_device(const double* d_amps, const double* d_u, int64_t n, double N, double mprime,
                             double prob_scale, uint8_t* d_accept, int64_t* d_count, void* stream) {
   SF_GUARD_BEGIN
@@ -360,9 +467,10 @@ int sf_overlap_device(const double* a, const double* b, int64_t n, double* out, 
   SF_GUARD_END
 }
 
-int sf_amplitudes(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel* sel, double* out,
-                  double* f_actual) {
-  SF_GUARD_BEGIN
+// The host-buffer forms: bitstrings in, amplitudes (prob = 0) or
+// probabilities (prob = 1, divided by f_actual when divide_by_f) out.
+static int host_form(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel* sel, double* out,
+                     double* f_actual, int prob, int divide_by_f) {
   if (!h || !sel) sf::fail(SF_EINVAL, "null argument");
   if (n < 0) sf::fail(SF_EINVAL, "negative bitstring count");
   if (n > 0 && (!bits || !out)) sf::fail(SF_EINVAL, "null host buffer");
@@ -393,17 +501,32 @@ int sf_amplitudes(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel
     hb.out = nullptr;
     hb.cap_n = 0;
     cuda_check(cudaMalloc(&hb.bits, (size_t)n * 8), "cudaMalloc bitstrings");
-    cuda_check(cudaMalloc(&hb.out, (size_t)n * 16), "cudaMalloc output");
+    cuda_check(cudaMalloc(&hb.out, (size_t)n * 24), "cudaMalloc output");
     hb.cap_n = n;
   }
   cuda_check(cudaMemcpyAsync(hb.bits, bits, (size_t)n * 8, cudaMemcpyHostToDevice, hst), "cudaMemcpyAsync");
   sf::exec_run(*h->p, hb.bits, n, *sel, hb.out, 0, hb.ws, hb.ws_bytes, hst, true);
-  cuda_check(cudaMemcpyAsync(out, hb.out, (size_t)n * 16, cudaMemcpyDeviceToHost, hst), "cudaMemcpyAsync");
-  cuda_check(cudaStreamSynchronize(hst), "cudaStreamSynchronize");
-  int flag = 0;
-  cuda_check(cudaMemcpy(&flag, h->p->d_err, sizeof(int), cudaMemcpyDeviceToHost), "cudaMemcpy");
-  if (flag) sf::fail(SF_ECUDA, "a kernel wait timed out (error flag set); results are invalid");
+  if (prob) {
+    sf::launch_prob(hb.out, n, divide_by_f ? (fa > 0 ? 1.0 / fa : 0.0) : 1.0, hb.probs(n), hst);
+    cuda_check(cudaMemcpyAsync(out, hb.probs(n), (size_t)n * 8, cudaMemcpyDeviceToHost, hst), "cudaMemcpyAsync");
+  } else {
+    cuda_check(cudaMemcpyAsync(out, hb.out, (size_t)n * 16, cudaMemcpyDeviceToHost, hst), "cudaMemcpyAsync");
+  }
+  sf::check_wait_flag(h->p->d_err, hst);
   return SF_OK;
+}
+
+int sf_amplitudes(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel* sel, double* out,
+                  double* f_actual) {
+  SF_GUARD_BEGIN
+  return host_form(h, bits, n, sel, out, f_actual, 0, 0);
+  SF_GUARD_END
+}
+
+int sf_probabilities(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_sel* sel, int divide_by_f,
+                     double* out, double* f_actual) {
+  SF_GUARD_BEGIN
+  return host_form(h, bits, n, sel, out, f_actual, 1, divide_by_f);
   SF_GUARD_END
 }
 

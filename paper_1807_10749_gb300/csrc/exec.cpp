@@ -146,7 +146,10 @@ int cached_depths(const Plan& p) {
   return p.merged_last ? nL - 1 : nL;
 }
 
-Layout make_layout(const Plan& p, uint64_t n_finals, const Compact& cp, int64_t budget_override = 0) {
+// extra: fixed bytes after the rest (the compensation terms of
+// SF_PREC_COMPENSATED), counted against the budget.
+Layout make_layout(const Plan& p, uint64_t n_finals, const Compact& cp, int64_t budget_override = 0,
+                   size_t extra = 0) {
   const int nL = cached_depths(p);
   const size_t nb = node_bytes(p);
   int64_t budget = budget_override > 0 ? budget_override : p.opts.hbm_budget_bytes;
@@ -165,8 +168,8 @@ Layout make_layout(const Plan& p, uint64_t n_finals, const Compact& cp, int64_t 
       if (s < nL) cum += p.levels[s].bits;
     }
     // compact finals when they fit: smaller blocks first, dense finals last
-    const size_t dense = tot * nb;
-    const size_t withc = align256(dense) + cp.fixed + (size_t)B * cp.per_final;
+    const size_t dense = align256(tot * nb) + extra;
+    const size_t withc = align256(tot * nb) + cp.fixed + (size_t)B * cp.per_final + extra;
     const bool fits_c = cp.any() && (int64_t)withc <= budget;
     if (fits_c || (!cp.any() && (int64_t)dense <= budget) || B == 1) {
       lay.B = (int)B;
@@ -329,11 +332,101 @@ double segment_bytes(const SegmentPlan& s) {
   return b;
 }
 
-size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget) {
-  double fa;
-  auto rs = select_ranges(p, s, &fa);
-  Layout lay = make_layout(p, count_finals(p, rs), compact_plan(p, n), budget);
+namespace {
+
+// The union of the requests' selected ranges (sorted, disjoint, merged).
+std::vector<Range> union_ranges(const std::vector<ExecReq>& reqs) {
+  std::vector<Range> all;
+  for (auto& r : reqs)
+    if (r.n > 0) all.insert(all.end(), r.rs.begin(), r.rs.end());
+  std::sort(all.begin(), all.end(), [](const Range& x, const Range& y) { return x.lo < y.lo; });
+  std::vector<Range> out;
+  for (auto& r : all) {
+    if (r.hi <= r.lo) continue;
+    if (!out.empty() && r.lo <= out.back().hi) out.back().hi = std::max(out.back().hi, r.hi);
+    else out.push_back(r);
+  }
+  return out;
+}
+
+int64_t total_bits(const std::vector<ExecReq>& reqs) {
+  int64_t t = 0;
+  for (auto& r : reqs)
+    if (!r.rs.empty()) t += r.n;
+  return t;
+}
+
+size_t comp_bytes(const Plan& p, const std::vector<ExecReq>& reqs) {
+  if (p.opts.precision != SF_PREC_COMPENSATED) return 0;
+  size_t b = 0;
+  for (auto& r : reqs)
+    if (r.n > 0 && !r.rs.empty()) b += align256((size_t)r.n * 16);
+  return b;
+}
+
+// Finals of one request in path order: final id and its selected leaves.
+struct FinalCursor {
+  const std::vector<Range>* rs = nullptr;
+  int fb = 0;
+  size_t ri = 0;
+  uint64_t cur = 0;
+  bool has = false;
+  Final f{};
+  void start(const std::vector<Range>& r, int fbits) {
+    rs = &r;
+    fb = fbits;
+    ri = 0;
+    cur = r.empty() ? 0 : (r[0].lo >> fb);
+    advance();
+  }
+  void advance() {
+    has = false;
+    while (ri < rs->size()) {
+      const uint64_t lo = (*rs)[ri].lo, hi = (*rs)[ri].hi;
+      const uint64_t a = lo >> fb, b = (hi - 1) >> fb;
+      if (cur < a) cur = a;
+      if (cur > b) {
+        ri++;
+        continue;
+      }
+      f.fid = cur;
+      f.all = true;
+      std::memset(f.mask, 0, sizeof(f.mask));
+      if (fb > 0) {
+        const uint64_t glo = cur << fb, ghi = (cur + 1) << fb;
+        uint64_t cnt = 0;
+        // leaves of this final from every range that touches it
+        for (size_t r2 = ri; r2 < rs->size() && (*rs)[r2].lo < ghi; r2++) {
+          uint64_t l = std::max((*rs)[r2].lo, glo), h = std::min((*rs)[r2].hi, ghi);
+          for (uint64_t v = l; v < h; v++) {
+            uint64_t b2 = v - glo;
+            f.mask[b2 >> 6] |= 1ull << (b2 & 63);
+            cnt++;
+          }
+        }
+        f.all = cnt == (1ull << fb);
+      }
+      cur++;
+      has = true;
+      return;
+    }
+  }
+};
+
+}  // namespace
+
+size_t exec_workspace_bytes(const Plan& p, const std::vector<ExecReq>& reqs, int64_t budget) {
+  const std::vector<Range> u = union_ranges(reqs);
+  Layout lay = make_layout(p, count_finals(p, u), compact_plan(p, total_bits(reqs)), budget, comp_bytes(p, reqs));
   return lay.bytes + 256;
+}
+
+size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget) {
+  std::vector<ExecReq> one(1);
+  double fa;
+  one[0].rs = select_ranges(p, s, &fa);
+  one[0].n = n;
+  return exec_workspace_bytes(p, one, budget);
 }
 
 void prof_begin(Plan& p, int kind, double bytes, void* stream, void** e1_out, int launches) {
@@ -392,29 +485,47 @@ void exec_release_cache(Plan& p) {
 void exec_free_cache(void* c) { delete reinterpret_cast<Cache*>(c); }
 
 void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& sel, double* d_out,
-              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
+              int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache, ExecCtx* ctx) {
+  if (n < 0) fail(SF_EINVAL, "negative bitstring count");
+  std::vector<ExecReq> one(1);
+  double fa = 0;
+  one[0].rs = select_ranges(plan, sel, &fa);
+  one[0].d_bits = d_bits;
+  one[0].n = n;
+  one[0].d_out = d_out;
+  one[0].accumulate = accumulate;
+  one[0].cancel = ctx ? ctx->cancel : nullptr;
+  exec_run(plan, one, ws, ws_bytes, stream, keep_cache, ctx);
+}
+
+void exec_run(Plan& plan, std::vector<ExecReq>& reqs, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
               ExecCtx* ctx) {
   cudaStream_t st = (cudaStream_t)stream;
   void** cache_slot = (ctx && ctx->cache_slot) ? ctx->cache_slot : &plan.cache;
   const bool prof = ctx ? ctx->profile : true;
-  const volatile int* cancel = ctx ? ctx->cancel : nullptr;
   int* err = (ctx && ctx->err) ? ctx->err : plan.d_err;
-  const uint32_t* tabA = (ctx && ctx->tabA) ? ctx->tabA : plan.d_tabA;
-  const uint32_t* tabB = (ctx && ctx->tabB) ? ctx->tabB : plan.d_tabB;
+  const uint32_t* tabA = plan.d_tabA;
+  const uint32_t* tabB = plan.d_tabB;
   const int64_t budget = ctx ? ctx->budget : 0;
-  double fa = 0;
-  std::vector<Range> rs = select_ranges(plan, sel, &fa);
-  if (n < 0) fail(SF_EINVAL, "negative bitstring count");
-  if (!accumulate) {
-    void* e1 = nullptr;
-    if (prof) prof_begin(plan, 2, 16.0 * n, st, &e1);
-    launch_zero(d_out, 2 * n, st);
-    if (prof) prof_end(plan, e1, st);
+  const bool compensated = plan.opts.precision == SF_PREC_COMPENSATED;
+  for (auto& r : reqs) {
+    if (r.n < 0) fail(SF_EINVAL, "negative bitstring count");
+    r.cancelled = false;
+    if (r.n > 0 && !r.accumulate) {
+      void* e1 = nullptr;
+      if (prof) prof_begin(plan, 2, 16.0 * r.n, st, &e1);
+      launch_zero(r.d_out, 2 * r.n, st);
+      if (prof) prof_end(plan, e1, st);
+    }
   }
-  if (n == 0 || rs.empty()) return;
-  const uint64_t nfin = count_finals(plan, rs);
-  const Compact cp = compact_plan(plan, n);
-  Layout lay = make_layout(plan, nfin, cp, budget);
+  const std::vector<Range> urs = union_ranges(reqs);
+  const int64_t ntot = total_bits(reqs);
+  if (ntot == 0 || urs.empty()) return;
+  if (!tabA || !tabB || !err) fail(SF_EINVAL, "internal: plan has no device state");
+  const uint64_t nfin = count_finals(plan, urs);
+  const Compact cp = compact_plan(plan, ntot);
+  const size_t cb = comp_bytes(plan, reqs);
+  Layout lay = make_layout(plan, nfin, cp, budget, cb);
   const size_t nb = node_bytes(plan);
   const size_t need = lay.bytes + 256;
   if (!ws || ws_bytes < need)
@@ -454,8 +565,19 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
   const SegmentPlan& finB =
       plan.merged_last ? plan.B.last_merged : (plan.deferred ? plan.B.last_deferred : plan.B.seg[nL]);
 
+  // compensation terms of each request (after everything else), zeroed
+  char* comp_at = base + (lay.bytes - cb);
+  std::vector<double*> comp(reqs.size(), nullptr);
+  if (compensated)
+    for (size_t q = 0; q < reqs.size(); q++) {
+      if (reqs[q].n <= 0 || reqs[q].rs.empty()) continue;
+      comp[q] = reinterpret_cast<double*>(comp_at);
+      comp_at += align256((size_t)reqs[q].n * 16);
+      launch_zero(comp[q], 2 * reqs[q].n, st);
+    }
+
   // compact finals: block maps after the node slots, then B finals' buffers;
-  // the maps are built once per call from the bitstrings
+  // the maps are built once per call from every request's bitstrings
   uint32_t* cmap[2] = {nullptr, nullptr};
   char* cfin = nullptr;
   const uint32_t* ccount[2] = {nullptr, nullptr};
@@ -465,16 +587,14 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
     std::memset(&M, 0, sizeof(M));
     M.tab[0] = tabA;
     M.tab[1] = tabB;
-    M.bits = d_bits;
-    M.n = n;
     uint32_t* cnt = nullptr;
     if (prof && plan.d_cnt) {
       if (plan.cnt_seq > 0 && plan.cnt_seq % kCountRing == 0) prof_collect(plan);
       cnt = plan.d_cnt + 2 * (plan.cnt_seq % kCountRing);
       plan.cnt_seq++;
     }
-    double mb = 8.0 * (double)n;
-    int nk = 3;
+    double mb = 8.0 * (double)ntot;
+    int nk = 2;
     for (int side = 0; side < 2; side++) {
       if (!cp.s[side].on) continue;
       cmap[side] = reinterpret_cast<uint32_t*>(at);
@@ -490,24 +610,26 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
       nk++;
     }
     cfin = at;
+    std::vector<std::pair<const uint64_t*, int64_t>> sets;
+    for (auto& r : reqs)
+      if (r.n > 0 && !r.rs.empty()) {
+        sets.push_back({r.d_bits, r.n});
+        nk++;
+      }
     void* e1 = nullptr;
     if (prof) prof_begin(plan, 2, mb, st, &e1, nk);
-    launch_block_maps(M, st);
+    launch_block_maps(M, sets, st);
     if (prof) prof_end(plan, e1, st);
   }
   auto cbuf = [&](size_t i, int side) -> void* {
     return cfin + i * cp.per_final + (side && cp.s[0].on ? cp.s[0].buf_bytes : 0);
   };
 
-  // gather template
+  // gather template (per request: bits, n, acc, comp)
   GatherLaunch G;
   std::memset(&G, 0, sizeof(G));
   G.tabA = tabA;
   G.tabB = tabB;
-  G.bits = d_bits;
-  G.acc = d_out;
-  G.n = n;
-  G.accumulate = 1;
   G.g = plan.deferred ? plan.levels.back().n_cross : 0;
   G.nterm_bits = plan.deferred ? plan.cross[plan.levels.back().first_cross].bits : 0;
   for (int side = 0; side < 2; side++) {
@@ -540,47 +662,43 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
     G.xbits[i] = (uint8_t)plan.cross[i].bits;
   }
 
-  // enumerate finals in order
-  std::vector<Final> block;
-  size_t ri = 0;
-  uint64_t cur = rs.empty() ? 0 : (rs[0].lo >> fb);
-  auto next_final = [&](Final& f) -> bool {
-    while (ri < rs.size()) {
-      const uint64_t lo = rs[ri].lo, hi = rs[ri].hi;
-      const uint64_t a = lo >> fb, b = (hi - 1) >> fb;
-      if (cur < a) cur = a;
-      if (cur > b) {
-        ri++;
-        continue;
+  // finals of the union in path order; per final, the requests that select
+  // leaves of it (and which)
+  std::vector<FinalCursor> cur(reqs.size());
+  for (size_t q = 0; q < reqs.size(); q++) {
+    if (reqs[q].n > 0) cur[q].start(reqs[q].rs, fb);
+  }
+  struct UFinal {
+    uint64_t fid;
+    std::vector<std::pair<int, Final>> who;
+  };
+  auto next_final = [&](UFinal& u) -> bool {
+    uint64_t best = ~0ull;
+    for (auto& c : cur)
+      if (c.rs && c.has) best = std::min(best, c.f.fid);
+    if (best == ~0ull) return false;
+    u.fid = best;
+    u.who.clear();
+    for (size_t q = 0; q < cur.size(); q++)
+      if (cur[q].rs && cur[q].has && cur[q].f.fid == best) {
+        u.who.push_back({(int)q, cur[q].f});
+        cur[q].advance();
       }
-      f.fid = cur;
-      f.all = true;
-      std::memset(f.mask, 0, sizeof(f.mask));
-      if (fb > 0) {
-        const uint64_t glo = cur << fb, ghi = (cur + 1) << fb;
-        uint64_t cnt = 0;
-        // collect leaves of this final from every range that touches it
-        for (size_t r2 = ri; r2 < rs.size() && rs[r2].lo < ghi; r2++) {
-          uint64_t l = std::max(rs[r2].lo, glo), h = std::min(rs[r2].hi, ghi);
-          for (uint64_t v = l; v < h; v++) {
-            uint64_t b2 = v - glo;
-            f.mask[b2 >> 6] |= 1ull << (b2 & 63);
-            cnt++;
-          }
-        }
-        f.all = cnt == (1ull << fb);
-      }
-      cur++;
-      return true;
-    }
-    return false;
+    return true;
   };
 
+  std::vector<UFinal> block;
+  std::vector<std::vector<GatherFinal>> gf(reqs.size());
   try {
-    Final f;
+    UFinal f;
     bool more = next_final(f);
     while (more) {
-      if (cancel && *cancel) fail(SF_ECANCELLED, "request cancelled");
+      int live = 0;
+      for (auto& r : reqs) {
+        if (r.cancel && *r.cancel) r.cancelled = true;
+        if (r.n > 0 && !r.rs.empty() && !r.cancelled) live++;
+      }
+      if (live == 0) fail(SF_ECANCELLED, "request cancelled");
       block.clear();
       while (more && (int)block.size() < lay.B) {
         block.push_back(f);
@@ -662,7 +780,7 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
       }
       // finals
       std::vector<Job> jobsA, jobsB;
-      std::vector<GatherFinal> gf;
+      for (auto& v : gf) v.clear();
       CompactOut coA, coB;
       for (int side = 0; side < 2; side++) {
         CompactOut& co = side ? coB : coA;
@@ -687,7 +805,10 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         }
         bool dead = pdead || dead_by_pins(finA.passes[0].dev, plan, fpath) ||
                     dead_by_pins(finB.passes[0].dev, plan, fpath);
-        if (dead) continue;
+        bool wanted = false;  // by a request that is still live
+        for (auto& w : block[i].who)
+          if (!reqs[w.first].cancelled) wanted = true;
+        if (dead || !wanted) continue;
         const size_t fs = C->final_first + i;
         jobsA.push_back({inA, bufA(fs), fpath});
         jobsB.push_back({inB, bufB(fs), fpath});
@@ -707,9 +828,12 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
         cd sc = psa * finA.scale * psb * finB.scale;
         g.sre = sc.real();
         g.sim = sc.imag();
-        g.all_leaves = block[i].all ? 1 : 0;
-        std::memcpy(g.leafmask, block[i].mask, sizeof(g.leafmask));
-        gf.push_back(g);
+        for (auto& w : block[i].who) {
+          if (reqs[w.first].cancelled) continue;
+          g.all_leaves = w.second.all ? 1 : 0;
+          std::memcpy(g.leafmask, w.second.mask, sizeof(g.leafmask));
+          gf[w.first].push_back(g);
+        }
       }
       run_segment(*C, plan, finA, jobsA, st, prof, err, cmap[0] ? &coA : nullptr);
       run_segment(*C, plan, finB, jobsB, st, prof, err, cmap[1] ? &coB : nullptr);
@@ -723,17 +847,33 @@ void exec_run(Plan& plan, const uint64_t* d_bits, int64_t n, const sf_path_sel& 
           cum += plan.levels[s].bits;
         }
       }
-      for (size_t g0 = 0; g0 < gf.size(); g0 += GATHER_FINALS) {
-        size_t g1 = std::min(gf.size(), g0 + GATHER_FINALS);
-        G.n_finals = (int)(g1 - g0);
-        for (size_t j = g0; j < g1; j++) G.finals[j - g0] = gf[j];
-        void* e1 = nullptr;
-        const double gb = (double)n * (8.0 + 32.0 + 16.0 * G.n_finals * (2 << G.g));
-        if (prof) prof_begin(plan, 1, gb, st, &e1);
-        launch_gather(G, st);
-        if (prof) prof_end(plan, e1, st);
+      for (size_t q = 0; q < reqs.size(); q++) {
+        const ExecReq& r = reqs[q];
+        if (gf[q].empty() || r.cancelled) continue;
+        G.bits = r.d_bits;
+        G.n = r.n;
+        G.acc = r.d_out;
+        G.comp = comp[q];
+        for (size_t g0 = 0; g0 < gf[q].size(); g0 += GATHER_FINALS) {
+          size_t g1 = std::min(gf[q].size(), g0 + GATHER_FINALS);
+          G.n_finals = (int)(g1 - g0);
+          for (size_t j = g0; j < g1; j++) G.finals[j - g0] = gf[q][j];
+          void* e1 = nullptr;
+          const double gb = (double)r.n * (8.0 + 32.0 + 16.0 * G.n_finals * (2 << G.g));
+          if (prof) prof_begin(plan, 1, gb, st, &e1);
+          launch_gather(G, st);
+          if (prof) prof_end(plan, e1, st);
+        }
       }
     }
+    if (compensated)
+      for (size_t q = 0; q < reqs.size(); q++)
+        if (comp[q] && !reqs[q].cancelled) {
+          void* e1 = nullptr;
+          if (prof) prof_begin(plan, 2, 48.0 * reqs[q].n, st, &e1);
+          launch_fold(reqs[q].d_out, comp[q], 2 * reqs[q].n, st);
+          if (prof) prof_end(plan, e1, st);
+        }
   } catch (...) {
     for (auto& v : C->slots)
       for (auto& sl : v) sl.valid = false;

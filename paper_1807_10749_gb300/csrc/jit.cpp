@@ -24,6 +24,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -193,6 +194,221 @@ void gen_copy(std::ostringstream& o, const PassPlan& pp) {
   o << "}\n";
 }
 
+// ---- packed complex stages ----------------------------------------------
+// A register slot holds one complex amplitude in an FP32x2 register pair r.
+// At generation time each slot carries a map M, a signed permutation of the
+// pair: value (re, im) = M (r.x, r.y). Multiplying a value by i^k changes
+// only M (M <- J^k M, J = [[0,-1],[1,0]]), so the Google gates' factors +-1,
+// +-i and the even powers of e^{i pi/4} of the phase groups cost nothing. A
+// butterfly out = c_a a + c_b b (c in {+-1, +-i}) is one packed add when the
+// two terms' maps C(c_a) M_a and C(c_b) M_b have the same pattern (both
+// diagonal or both anti-diagonal): r_out = r_a + D r_b, D = (C(c_a) M_a)^T
+// C(c_b) M_b diagonal, with the map C(c_a) M_a; otherwise r_b is swapped first
+// (two moves), which costs what the scalar form costs. Odd powers of
+// e^{i pi/4}, the per-thread phase and the post scale act on the register
+// pair with the map folded in; stores write the plain (re, im) layout.
+struct M2 {
+  int a[2][2];
+};
+M2 m2_id() { return M2{{{1, 0}, {0, 1}}}; }
+M2 m2_mul(const M2& x, const M2& y) {
+  M2 r{};
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) r.a[i][j] = x.a[i][0] * y.a[0][j] + x.a[i][1] * y.a[1][j];
+  return r;
+}
+M2 m2_t(const M2& x) { return M2{{{x.a[0][0], x.a[1][0]}, {x.a[0][1], x.a[1][1]}}}; }  // inverse of a signed permutation
+M2 m2_ipow(int k) {  // i^k as a real 2x2 matrix
+  M2 J{{{0, -1}, {1, 0}}}, r = m2_id();
+  for (int t = 0; t < (k & 3); t++) r = m2_mul(J, r);
+  return r;
+}
+bool m2_anti(const M2& x) { return x.a[0][0] == 0; }
+const M2 kSwap{{{0, 1}, {1, 0}}};
+
+std::string pair_lit(int x, int y) {
+  return "make_float2(" + std::string(x < 0 ? "-1.f" : "1.f") + ", " + (y < 0 ? "-1.f" : "1.f") + ")";
+}
+
+// Emit r_out = r_a + D r_b (D diagonal, entries +-1).
+std::string cadd_expr(const std::string& ra, const std::string& rb, const M2& D) {
+  if (D.a[0][0] == 1 && D.a[1][1] == 1) return "__fadd2_rn(" + ra + ", " + rb + ")";
+  return "__ffma2_rn(" + rb + ", " + pair_lit(D.a[0][0], D.a[1][1]) + ", " + ra + ")";
+}
+
+// A packed-complex register stage (gates H, X^1/2, Y^1/2 and phase groups).
+void gen_stage_cpack(std::ostringstream& o, const PassPlan& pp, const DevStage& st, int R, bool last,
+                     const std::function<std::string(int)>& at, int j0) {
+  const DevPass& d = pp.dev;
+  const int NR = 1 << R;
+  std::vector<M2> M(NR, m2_id());
+  o << "float2 v[" << NR << "];\n";
+  if (j0 >= 0) {
+    for (int i = 0; i < NR; i++) {
+      if ((i >> j0) & 1) continue;
+      const int i1 = i | (1 << j0);
+      o << "{ const float4 q = *reinterpret_cast<const float4*>(" << at(i) << "); v[" << i
+        << "] = make_float2(q.x, q.y); v[" << i1 << "] = make_float2(q.z, q.w); }\n";
+    }
+  } else {
+    for (int i = 0; i < NR; i++) o << "v[" << i << "] = *(" << at(i) << ");\n";
+  }
+  o << "int kst = 0;\n";
+  bool kst = false;
+  auto V = [](int i) { return "v[" + std::to_string(i) + "]"; };
+  // r' = h (r + t J r): the value times e^{i pi/4} with the map M kept
+  auto omega1 = [&](int i) {
+    const M2 T = m2_mul(m2_t(M[i]), m2_mul(m2_ipow(1), M[i]));  // M^T J M = t J
+    const int t = T.a[1][0];
+    o << "{ const float2 r = " << V(i) << "; " << V(i) << " = __ffma2_rn(make_float2(r.y, r.x), make_float2("
+      << (t > 0 ? "-" : "") << "0.70710678118654752f, " << (t > 0 ? "" : "-")
+      << "0.70710678118654752f), __fmul2_rn(r, make_float2(0.70710678118654752f, 0.70710678118654752f))); }\n";
+  };
+  for (int oi = st.op_begin; oi < st.op_end; oi++) {
+    const DevOp& op = pp.ops[oi];
+    if (op.code == DOP_H || op.code == DOP_XH || op.code == DOP_YH) {
+      // out0 = c0 a + c1 b, out1 = c2 a + c3 b as powers of i (+-1: 0 / 2, -i: 3)
+      int c[4];
+      if (op.code == DOP_H) c[0] = 0, c[1] = 0, c[2] = 0, c[3] = 2;
+      else if (op.code == DOP_XH) c[0] = 0, c[1] = 3, c[2] = 3, c[3] = 0;
+      else c[0] = 0, c[1] = 2, c[2] = 0, c[3] = 0;
+      const int J = op.a;
+      for (int i0 = 0; i0 < NR; i0++) {
+        if ((i0 >> J) & 1) continue;
+        const int i1 = i0 | (1 << J);
+        const M2 Qa0 = m2_mul(m2_ipow(c[0]), M[i0]), Qb0 = m2_mul(m2_ipow(c[1]), M[i1]);
+        const M2 Qa1 = m2_mul(m2_ipow(c[2]), M[i0]), Qb1 = m2_mul(m2_ipow(c[3]), M[i1]);
+        const bool sw0 = m2_anti(Qa0) != m2_anti(Qb0), sw1 = m2_anti(Qa1) != m2_anti(Qb1);
+        o << "{ const float2 a = " << V(i0) << ", b = " << V(i1) << ";";
+        if (sw0 || sw1) o << " const float2 bs = make_float2(b.y, b.x);";
+        const M2 D0 = m2_mul(m2_t(Qa0), sw0 ? m2_mul(Qb0, kSwap) : Qb0);
+        const M2 D1 = m2_mul(m2_t(Qa1), sw1 ? m2_mul(Qb1, kSwap) : Qb1);
+        o << " " << V(i0) << " = " << cadd_expr("a", sw0 ? "bs" : "b", D0) << "; " << V(i1) << " = "
+          << cadd_expr("a", sw1 ? "bs" : "b", D1) << "; }\n";
+        M[i0] = Qa0;
+        M[i1] = Qa1;
+      }
+      continue;
+    }
+    if (op.code != DOP_PHASE) fail(SF_EINVAL, "internal: op without a packed complex form");
+    const DevPhaseGroup& G = pp.phases[op.arg];
+    for (int j = 0; j < R; j++)
+      for (int l = 0; l < R; l++)
+        if (((G.czq[j] >> l) & 1) != ((G.czq[l] >> j) & 1))
+          fail(SF_EINVAL, "internal: asymmetric CZ partners in a phase group");
+    o << "{ // phase group " << op.arg << "\n";
+    for (int i = 0; i < NR; i++) {  // plan-static part
+      int ku = 0;
+      for (int j = 0; j < R; j++)
+        if ((i >> j) & 1) {
+          ku += G.wstat[j];
+          for (int l = j + 1; l < R; l++)
+            if (((i >> l) & 1) && ((G.czq[j] >> l) & 1)) ku += 4;
+        }
+      ku &= 7;
+      M[i] = m2_mul(m2_ipow(ku >> 1), M[i]);
+      if (ku & 1) omega1(i);
+    }
+    char b[160];
+    auto kadd = [&](const std::string& e) {
+      o << "kst += " << e << ";\n";
+      kst = true;
+    };
+    if (G.m1) std::snprintf(b, sizeof b, "__popc(gfix & 0x%xu)", G.m1), kadd(b);
+    if (G.m2) std::snprintf(b, sizeof b, "2 * __popc(gfix & 0x%xu)", G.m2), kadd(b);
+    if (G.m4) std::snprintf(b, sizeof b, "4 * __popc(gfix & 0x%xu)", G.m4), kadd(b);
+    for (int cc = 0; cc < G.nsh; cc++) {
+      std::snprintf(b, sizeof b, "4 * __popc(gfix & (gfix >> %d) & 0x%xu)", G.sh[cc], G.shm[cc]);
+      kadd(b);
+    }
+    std::string wr[MAX_R];
+    bool sign_only[MAX_R];
+    for (int j = 0; j < R; j++) {
+      sign_only[j] = true;
+      if (G.czf[j]) {
+        std::snprintf(b, sizeof b, "4 * __popc(gfix & 0x%xu)", G.czf[j]);
+        wr[j] = b;
+      }
+    }
+    for (int si = 0; si < G.nsel; si++) {
+      const auto& e = G.sel[si];
+      std::string dg = e.xi >= 0 ? "digit_of(P.xshift, P.xbits, g.path, " + std::to_string(e.xi) + ")" : "0";
+      std::snprintf(b, sizeof b, "(int)(0x%xu >> (8 * %s) & 0xffu)",
+                    (uint32_t)e.w[0] | (uint32_t)e.w[1] << 8 | (uint32_t)e.w[2] << 16 | (uint32_t)e.w[3] << 24,
+                    dg.c_str());
+      if (e.reg >= 0) {
+        if (!wr[e.reg].empty()) wr[e.reg] += " + ";
+        wr[e.reg] += b;
+        for (int dd = 0; dd < 4; dd++)
+          if (e.w[dd] & 3) sign_only[e.reg] = false;
+      } else {
+        kadd(std::string(b) + " * (int)((gfix >> " + std::to_string(e.pos) + ") & 1u)");
+      }
+    }
+    for (int j = 0; j < R; j++) {  // per-thread / per-path weights of register bits
+      if (wr[j].empty()) continue;
+      o << "{ const int w = " << wr[j] << ";\n";
+      if (sign_only[j]) {
+        o << "const float sg = (w & 4) ? -1.f : 1.f; const float2 sg2 = make_float2(sg, sg);\n";
+        for (int i = 0; i < NR; i++)
+          if ((i >> j) & 1) o << V(i) << " = __fmul2_rn(" << V(i) << ", sg2);\n";
+      } else {
+        // value * f = M r * f:  r' = fx r + fy (M^T J M) r
+        o << "const float2 f = w8[w & 7]; const float2 fxx = make_float2(f.x, f.x), fpy = make_float2(-f.y, f.y), "
+             "fny = make_float2(f.y, -f.y);\n";
+        for (int i = 0; i < NR; i++) {
+          if (!((i >> j) & 1)) continue;
+          const M2 T = m2_mul(m2_t(M[i]), m2_mul(m2_ipow(1), M[i]));
+          o << "{ const float2 r = " << V(i) << "; " << V(i) << " = __ffma2_rn(make_float2(r.y, r.x), "
+            << (T.a[1][0] > 0 ? "fpy" : "fny") << ", __fmul2_rn(r, fxx)); }\n";
+        }
+      }
+      o << "}\n";
+    }
+    o << "}\n";
+  }
+  // the stage's end: the per-thread phase e^{i pi kst/4} and the post scale,
+  // with every slot's map folded in, so the registers hold (re, im)
+  const bool scale = last && d.post_scale != 1.0f;
+  if (kst) {
+    o << "{ float2 f = w8[kst & 7];\n";
+    if (scale) o << "f.x *= " << flit(d.post_scale) << "; f.y *= " << flit(d.post_scale) << ";\n";
+  } else {
+    o << "{\n";
+  }
+  for (int i = 0; i < NR; i++) {
+    const M2& m = M[i];
+    const bool anti = m2_anti(m);
+    const int s0 = anti ? m.a[0][1] : m.a[0][0], s1 = anti ? m.a[1][0] : m.a[1][1];
+    // value = (s0 c0, s1 c1), (c0, c1) = anti ? (r.y, r.x) : (r.x, r.y)
+    const std::string src = anti ? "make_float2(" + V(i) + ".y, " + V(i) + ".x)" : V(i);
+    const std::string sgn0 = s0 < 0 ? "-" : "", sgn1 = s1 < 0 ? "-" : "";
+    if (kst) {
+      // f * value: (fx c0' - fy c1', fy c0' + fx c1') with c' the signed components
+      o << "{ const float2 c = " << src << "; " << V(i) << " = __ffma2_rn(make_float2(c.y, c.x), make_float2("
+        << (s1 < 0 ? "" : "-") << "f.y, " << sgn0 << "f.y), __fmul2_rn(c, make_float2(" << sgn0 << "f.x, " << sgn1
+        << "f.x))); }\n";
+    } else if (scale) {
+      o << V(i) << " = __fmul2_rn(" << src << ", make_float2(" << sgn0 << flit(d.post_scale) << ", " << sgn1
+        << flit(d.post_scale) << "));\n";
+    } else if (anti || s0 < 0 || s1 < 0) {
+      if (s0 < 0 || s1 < 0) o << V(i) << " = __fmul2_rn(" << src << ", " << pair_lit(s0, s1) << ");\n";
+      else o << V(i) << " = " << src << ";\n";
+    }
+  }
+  o << "}\n(void)kst;\n";
+  if (j0 >= 0) {
+    for (int i = 0; i < NR; i++) {
+      if ((i >> j0) & 1) continue;
+      const int i1 = i | (1 << j0);
+      o << "*reinterpret_cast<float4*>(" << at(i) << ") = make_float4(" << V(i) << ".x, " << V(i) << ".y, " << V(i1)
+        << ".x, " << V(i1) << ".y);\n";
+    }
+  } else {
+    for (int i = 0; i < NR; i++) o << "*(" << at(i) << ") = " << V(i) << ";\n";
+  }
+}
+
 // One pass as a stage program: struct `name`_prog in namespace sf and an
 // extern "C" kernel `name`.
 std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
@@ -215,36 +431,15 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
       C[i] = c;
     }
     for (int j = 0; j < R; j++) gr[j] = d.gpos[st.rbit[j]];
-    // Packed form (FP32x2): stages of H, X^1/2, Y^1/2 and phase groups only.
-    // Register bit p (the one with the fewest non-diagonal gates) pairs the
-    // amplitudes: Vr[s] = (re of lane 0, re of lane 1), Vi[s] likewise, so a
-    // butterfly on any other register bit is 4 FP32x2 adds per 4 amplitudes.
-    bool packed = pack && R >= 2;
-    int cnt[MAX_R] = {0};
+    // packed complex form (FP32x2): stages of H, X^1/2, Y^1/2 and phase groups
+    bool packed = pack;
     for (int oi = st.op_begin; oi < st.op_end && packed; oi++) {
-      const DevOp& op = pp.ops[oi];
-      if (op.code == DOP_H || op.code == DOP_XH || op.code == DOP_YH) cnt[op.a]++;
-      else if (op.code != DOP_PHASE) packed = false;
+      const int c = pp.ops[oi].code;
+      if (c != DOP_H && c != DOP_XH && c != DOP_YH && c != DOP_PHASE) packed = false;
     }
-    int p = 0;
-    for (int j = 1; j < R; j++)
-      if (cnt[j] < cnt[p]) p = j;
-    auto slot = [&](int i) { return (i & ((1 << p) - 1)) | ((i >> (p + 1)) << p); };
-    auto RE = [&](int i) {
-      return packed ? "Vr[" + std::to_string(slot(i)) + "]." + (((i >> p) & 1) ? "y" : "x")
-                    : "v[" + std::to_string(i) + "].x";
-    };
-    auto IM = [&](int i) {
-      return packed ? "Vi[" + std::to_string(slot(i)) + "]." + (((i >> p) & 1) ? "y" : "x")
-                    : "v[" + std::to_string(i) + "].y";
-    };
     o << "if (active) { // stage " << s << (packed ? " (packed)" : "") << "\n";
     o << "const uint32_t pf = swz(" << deposit(st.tpos, k - R) << ");\n";
     o << "const uint32_t gfix = g.base | " << deposit(st.tg, k - R) << ";\n(void)gfix;\n";
-    if (packed)
-      o << "float2 Vr[" << NR / 2 << "], Vi[" << NR / 2 << "];\nconst float2 M1 = make_float2(-1.f, -1.f);\n(void)M1;\n";
-    else
-      o << "float2 v[" << NR << "];\n";
     // Addresses pf ^ C_i: the swizzle only touches bits 1..3, so with
     // pf = ph | pl and C_i = h_i | l_i split at bit 4, pf ^ C_i =
     // (ph | (pl ^ l_i)) + h_i. One base pointer per distinct low part l, and a
@@ -267,6 +462,14 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
     int j0 = -1;
     for (int j = 0; j < R; j++)
       if (st.rbit[j] == 0) j0 = j;
+    if (packed) {
+      gen_stage_cpack(o, pp, st, R, s == d.n_stages - 1, at, j0);
+      o << "}\ncompute_bar(ncomp);\n";
+      continue;
+    }
+    auto RE = [&](int i) { return "v[" + std::to_string(i) + "].x"; };
+    auto IM = [&](int i) { return "v[" + std::to_string(i) + "].y"; };
+    o << "float2 v[" << NR << "];\n";
     if (j0 >= 0) {
       for (int i = 0; i < NR; i++) {
         if ((i >> j0) & 1) continue;
@@ -274,9 +477,6 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
         o << "{ const float4 q = *reinterpret_cast<const float4*>(" << at(i) << "); " << RE(i) << " = q.x; "
           << IM(i) << " = q.y; " << RE(i1) << " = q.z; " << IM(i1) << " = q.w; }\n";
       }
-    } else if (packed) {
-      for (int i = 0; i < NR; i++)
-        o << "{ const float2 t = *(" << at(i) << "); " << RE(i) << " = t.x; " << IM(i) << " = t.y; }\n";
     } else {
       for (int i = 0; i < NR; i++) o << "v[" << i << "] = *(" << at(i) << ");\n";
     }
@@ -284,43 +484,6 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
     o << "int kst = 0;\n";
     for (int oi = st.op_begin; oi < st.op_end; oi++) {
       const DevOp& op = pp.ops[oi];
-      if (packed && (op.code == DOP_H || op.code == DOP_XH || op.code == DOP_YH)) {
-        if (op.a == p) {  // within the pairs: scalar on the components
-          for (int i0 = 0; i0 < NR; i0++) {
-            if ((i0 >> p) & 1) continue;
-            const int i1 = i0 | (1 << p);
-            o << "{ const float ar = " << RE(i0) << ", ai = " << IM(i0) << ", br = " << RE(i1) << ", bi = " << IM(i1)
-              << "; ";
-            if (op.code == DOP_H)
-              o << RE(i0) << " = ar + br; " << IM(i0) << " = ai + bi; " << RE(i1) << " = ar - br; " << IM(i1)
-                << " = ai - bi; }\n";
-            else if (op.code == DOP_XH)
-              o << RE(i0) << " = ar + bi; " << IM(i0) << " = ai - br; " << RE(i1) << " = br + ai; " << IM(i1)
-                << " = bi - ar; }\n";
-            else
-              o << RE(i0) << " = ar - br; " << IM(i0) << " = ai - bi; " << RE(i1) << " = ar + br; " << IM(i1)
-                << " = ai + bi; }\n";
-          }
-        } else {  // across slots: FP32x2 butterflies (b * -1 + a is exact a - b)
-          const int jb = op.a < p ? op.a : op.a - 1;
-          for (int s0 = 0; s0 < NR / 2; s0++) {
-            if ((s0 >> jb) & 1) continue;
-            const std::string S0 = std::to_string(s0), S1 = std::to_string(s0 | (1 << jb));
-            o << "{ const float2 ar = Vr[" << S0 << "], ai = Vi[" << S0 << "], br = Vr[" << S1 << "], bi = Vi[" << S1
-              << "]; ";
-            if (op.code == DOP_H)
-              o << "Vr[" << S0 << "] = __fadd2_rn(ar, br); Vi[" << S0 << "] = __fadd2_rn(ai, bi); Vr[" << S1
-                << "] = __ffma2_rn(br, M1, ar); Vi[" << S1 << "] = __ffma2_rn(bi, M1, ai); }\n";
-            else if (op.code == DOP_XH)
-              o << "Vr[" << S0 << "] = __fadd2_rn(ar, bi); Vi[" << S0 << "] = __ffma2_rn(br, M1, ai); Vr[" << S1
-                << "] = __fadd2_rn(br, ai); Vi[" << S1 << "] = __ffma2_rn(ar, M1, bi); }\n";
-            else
-              o << "Vr[" << S0 << "] = __ffma2_rn(br, M1, ar); Vi[" << S0 << "] = __ffma2_rn(bi, M1, ai); Vr[" << S1
-                << "] = __fadd2_rn(ar, br); Vi[" << S1 << "] = __fadd2_rn(ai, bi); }\n";
-          }
-        }
-        continue;
-      }
       switch (op.code) {
         case DOP_H:
           o << "g_h<" << R << ", " << op.a << ">(v);\n";
@@ -453,17 +616,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
     }
     const bool last = s == d.n_stages - 1;
     const bool scale = last && d.post_scale != 1.0f;
-    if (packed && kst) {
-      o << "{ float2 f = w8[kst & 7];\n";
-      if (scale) o << "f.x *= " << flit(d.post_scale) << "; f.y *= " << flit(d.post_scale) << ";\n";
-      o << "const float2 C2 = make_float2(f.x, f.x), S2 = make_float2(f.y, f.y), N2 = make_float2(-f.y, -f.y);\n"
-        << "#pragma unroll\nfor (int q = 0; q < " << NR / 2 << "; q++) { const float2 r = Vr[q], m = Vi[q]; "
-        << "Vr[q] = __ffma2_rn(r, C2, __fmul2_rn(m, N2)); Vi[q] = __ffma2_rn(r, S2, __fmul2_rn(m, C2)); } }\n";
-    } else if (packed && scale) {
-      o << "{ const float2 P2 = make_float2(" << flit(d.post_scale) << ", " << flit(d.post_scale) << ");\n"
-        << "#pragma unroll\nfor (int q = 0; q < " << NR / 2
-        << "; q++) { Vr[q] = __fmul2_rn(Vr[q], P2); Vi[q] = __fmul2_rn(Vi[q], P2); } }\n";
-    } else if (kst) {
+    if (kst) {
       o << "{ float2 f = w8[kst & 7];\n";
       if (scale) o << "f.x *= " << flit(d.post_scale) << "; f.y *= " << flit(d.post_scale) << ";\n";
       o << "#pragma unroll\nfor (int i = 0; i < " << NR << "; i++) v[i] = cmul(v[i], f); }\n";
@@ -479,8 +632,6 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
         o << "*reinterpret_cast<float4*>(" << at(i) << ") = make_float4(" << RE(i) << ", " << IM(i) << ", " << RE(i1)
           << ", " << IM(i1) << ");\n";
       }
-    } else if (packed) {
-      for (int i = 0; i < NR; i++) o << "*(" << at(i) << ") = make_float2(" << RE(i) << ", " << IM(i) << ");\n";
     } else {
       for (int i = 0; i < NR; i++) o << "*(" << at(i) << ") = v[" << i << "];\n";
     }
@@ -635,37 +786,74 @@ void jit_prepare(Plan& p) {
 
 std::string jit_source(const PassPlan& pp) { return gen_pass(pp, kKernelName, true); }
 
+namespace {
+
+// Threads and dynamic shared memory of a pass launch (the generic kernel's
+// shape): stage warps + the two copy warps; three tile buffers, the run
+// offsets and the nine mbarriers.
+void pass_shape(const DevPass& d, int* threads, size_t* smem) {
+  const int nact = 1 << (d.k - d.R);
+  *threads = ((nact + 31) / 32) * 32 + 64;
+  const int nruns = 1 << (d.k - d.L);
+  *smem = 3 * ((size_t)8 << d.k) + 4 * (size_t)((nruns + 1) & ~1) + 9 * 8;
+}
+
+// Load the entry's library and kernel (caller holds g_mu), give it the
+// shared memory of a launch of this shape and compute its occupancy; the
+// attribute call loads the kernel into the current device's context.
+void ready_entry(Entry* e, int threads, size_t smem) {
+  if (!e->kern) {
+    cudaError_t rc = cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(rc));
+    rc = cudaLibraryGetKernel(&e->kern, e->lib, kKernelName);
+    if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(rc));
+  }
+  if (smem > e->smem_set) {
+    cudaError_t rc =
+        cudaFuncSetAttribute((const void*)e->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(rc));
+    e->smem_set = smem;
+    e->per_sm = 0;
+  }
+  if (!e->per_sm) {
+    int v = 0;
+    cudaError_t rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, (const void*)e->kern, threads, smem);
+    if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaOccupancy: ") + cudaGetErrorString(rc));
+    e->per_sm = v > 0 ? v : 1;
+  }
+}
+
+}  // namespace
+
+void jit_load(Plan& p) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (HalfPlan* h : {&p.A, &p.B}) {
+    std::vector<const PassPlan*> all;
+    for (auto& s : h->seg)
+      for (auto& pp : s.passes) all.push_back(&pp);
+    for (auto& pp : h->last_deferred.passes) all.push_back(&pp);
+    for (auto& pp : h->last_merged.passes) all.push_back(&pp);
+    for (const PassPlan* pp : all) {
+      if (pp->jit_id < 0) continue;
+      int threads;
+      size_t smem;
+      pass_shape(pp->dev, &threads, &smem);
+      ready_entry(static_cast<Entry*>(p.jit_entries[pp->jit_id]), threads, smem);
+    }
+  }
+}
+
 // Launch a pass with its specialised kernel; same launch shape as the
 // generic kernel.
 void launch_pass_jit(const PassLaunch& L, int tiles, void* entry, void* stream) {
   Entry* e = static_cast<Entry*>(entry);
-  const int tile_k = L.pass.k, R = L.pass.R;
-  const int nact = 1 << (tile_k - R);
-  const int threads = ((nact + 31) / 32) * 32 + 64;
-  const int nruns = 1 << (tile_k - L.pass.L);
-  const size_t smem = 3 * ((size_t)8 << tile_k) + 4 * (size_t)((nruns + 1) & ~1) + 9 * 8;
+  int threads;
+  size_t smem;
+  pass_shape(L.pass, &threads, &smem);
   int nb;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!e->kern) {
-      cudaError_t rc = cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(rc));
-      rc = cudaLibraryGetKernel(&e->kern, e->lib, kKernelName);
-      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(rc));
-    }
-    if (smem > e->smem_set) {
-      cudaError_t rc = cudaFuncSetAttribute((const void*)e->kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem);
-      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(rc));
-      e->smem_set = smem;
-      e->per_sm = 0;
-    }
-    if (!e->per_sm) {
-      int v = 0;
-      cudaError_t rc = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, (const void*)e->kern, threads, smem);
-      if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaOccupancy: ") + cudaGetErrorString(rc));
-      e->per_sm = v > 0 ? v : 1;
-    }
+    ready_entry(e, threads, smem);  // a no-op once jit_load ran on this device
     nb = e->per_sm;
   }
   int dev = 0, sms = 0;

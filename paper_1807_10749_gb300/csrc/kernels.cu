@@ -238,6 +238,16 @@ __global__ void __launch_bounds__(R >= 5 ? 320 : 576, 1) pass_kernel(const __gri
 }
 
 // ------------------------------------------------------------------ gather
+// s + x with the rounding error of the addition added to c (Neumaier's
+// variant of compensated summation, Numer. Math. 1974): IEEE round-to-nearest
+// additions only, no contraction.
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double x) {
+  const double t = __dadd_rn(s, x);
+  const double e = fabs(s) >= fabs(x) ? __dadd_rn(__dsub_rn(s, t), x) : __dadd_rn(__dsub_rn(x, t), s);
+  c = __dadd_rn(c, e);
+  s = t;
+}
+
 // Compact finals (CompactMap): part number of a layout index, and the slot
 // of a part (marked parts below it; every requested bitstring's parts are
 // marked).
@@ -296,7 +306,11 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       hb0 = compact_slot(P.B.c.cmap, p0) << P.B.c.ctl;
       if (P.B.c.csub1) hb1 = compact_slot(P.B.c.cmap, p0 | P.B.c.csub1) << P.B.c.ctl;
     }
-    double sr = 0.0, si = 0.0;
+    // Each final's contribution is added to the running FP64 sum in the
+    // order of the finals, starting from the accumulator itself, so the
+    // result does not depend on how finals are grouped into launches.
+    double sr = P.acc[2 * i], si = P.acc[2 * i + 1];
+    double cr = 0.0, ci = 0.0;  // compensation (P.comp != null)
     for (int f = 0; f < P.n_finals; f++) {
       const GatherFinal& F = P.finals[f];
       uint32_t pam = 0, pav = 0, pbm = 0, pbv = 0;
@@ -380,15 +394,21 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
           c = cadd(c, cmul(av, bv));
         }
       }
-      sr += (double)c.x * F.sre - (double)c.y * F.sim;
-      si += (double)c.x * F.sim + (double)c.y * F.sre;
+      const double tr = (double)c.x * F.sre - (double)c.y * F.sim;
+      const double ti = (double)c.x * F.sim + (double)c.y * F.sre;
+      if (P.comp) {
+        neumaier_add(sr, cr, tr);
+        neumaier_add(si, ci, ti);
+      } else {
+        sr += tr;
+        si += ti;
+      }
     }
-    if (P.accumulate) {
-      P.acc[2 * i] += sr;
-      P.acc[2 * i + 1] += si;
-    } else {
-      P.acc[2 * i] = sr;
-      P.acc[2 * i + 1] = si;
+    P.acc[2 * i] = sr;
+    P.acc[2 * i + 1] = si;
+    if (P.comp) {
+      P.comp[2 * i] += cr;
+      P.comp[2 * i + 1] += ci;
     }
   }
 }
@@ -512,6 +532,21 @@ __global__ void zero_kernel(double* p, int64_t n) {
     p[i] = 0.0;
 }
 
+// out += comp (the compensation terms of a compensated path sum).
+__global__ void fold_kernel(double* out, const double* comp, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __dadd_rn(out[i], comp[i]);
+}
+
+// Probabilities |a|^2 * scale (Section 3: p(x) = |<x|psi>|^2; scale = 1 or
+// 1 / f_actual), in exactly this operation order without contraction.
+__global__ void prob_kernel(const double* amps, int64_t n, double scale, double* probs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double re = amps[2 * i], im = amps[2 * i + 1];
+    probs[i] = __dmul_rn(__dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im)), scale);
+  }
+}
+
 // ------------------------------------------------------------- launchers
 static void check(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(SF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -605,7 +640,9 @@ void launch_gather(const GatherLaunch& L, void* stream) {
   check(cudaGetLastError(), "gather_kernel launch");
 }
 
-int launch_block_maps(const BlockMapLaunch& L, void* stream) {
+int launch_block_maps(const BlockMapLaunch& L0, const std::vector<std::pair<const uint64_t*, int64_t>>& sets,
+                      void* stream) {
+  BlockMapLaunch L = L0;
   cudaStream_t s = (cudaStream_t)stream;
   int launches = 0;
   int64_t maxw = 0;
@@ -617,7 +654,10 @@ int launch_block_maps(const BlockMapLaunch& L, void* stream) {
       maxw = std::max(maxw, L.nw[side]);
     }
   if (maxw == 0) return launches;
-  if (L.n > 0) {
+  for (auto& set : sets) {
+    if (set.second <= 0) continue;
+    L.bits = set.first;
+    L.n = set.second;
     const int64_t blocks = std::min<int64_t>((L.n + 255) / 256, (int64_t)num_sms() * 8);
     block_mark_kernel<<<(int)blocks, 256, 0, s>>>(L);
     check(cudaGetLastError(), "block_mark_kernel launch");
@@ -683,13 +723,56 @@ __global__ void overlap_kernel(const double* a, const double* b, int64_t n, doub
   }
 }
 
+// f_e = |<a|b>|^2 / (<a|a> <b|b>) from the four sums (Appendix C); 0 when
+// either norm is zero.
+__global__ void overlap_finish_kernel(double* out) {
+  const double den = out[2] * out[3];
+  out[4] = den > 0.0 ? (out[0] * out[0] + out[1] * out[1]) / den : 0.0;
+}
+
 void launch_overlap(const double* a, const double* b, int64_t n, double* out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  check(cudaMemsetAsync(out, 0, 4 * sizeof(double), s), "cudaMemsetAsync");
+  check(cudaMemsetAsync(out, 0, 5 * sizeof(double), s), "cudaMemsetAsync");
+  if (n > 0) {
+    int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 4);
+    overlap_kernel<<<(int)blocks, 256, 0, s>>>(a, b, n, out);
+    check(cudaGetLastError(), "overlap_kernel launch");
+  }
+  overlap_finish_kernel<<<1, 1, 0, s>>>(out);
+  check(cudaGetLastError(), "overlap_finish_kernel launch");
+}
+
+void launch_fold(double* out, const double* comp, int64_t n, void* stream) {
   if (n <= 0) return;
-  int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 4);
-  overlap_kernel<<<(int)blocks, 256, 0, s>>>(a, b, n, out);
-  check(cudaGetLastError(), "overlap_kernel launch");
+  int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  fold_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(out, comp, n);
+  check(cudaGetLastError(), "fold_kernel launch");
+}
+
+void launch_prob(const double* amps, int64_t n, double scale, double* probs, void* stream) {
+  if (n <= 0) return;
+  int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+  prob_kernel<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(amps, n, scale, probs);
+  check(cudaGetLastError(), "prob_kernel launch");
+}
+
+// Load every kernel of this library into the current device's context now
+// (CUDA loads modules lazily, on a kernel's first launch or query), so that
+// later calls - the fixed-scratch call in particular - load no code and
+// allocate no device memory for it.
+void preload_kernels() {
+  cudaFuncAttributes a;
+  const void* ks[] = {
+      (const void*)pass_kernel<1, false>, (const void*)pass_kernel<2, false>, (const void*)pass_kernel<3, false>,
+      (const void*)pass_kernel<4, false>, (const void*)pass_kernel<5, false>, (const void*)pass_kernel<1, true>,
+      (const void*)pass_kernel<2, true>,  (const void*)pass_kernel<3, true>,  (const void*)pass_kernel<4, true>,
+      (const void*)pass_kernel<5, true>,  (const void*)gather_kernel<0>,      (const void*)gather_kernel<1>,
+      (const void*)gather_kernel<2>,      (const void*)gather_kernel<3>,      (const void*)gather_kernel<4>,
+      (const void*)frugal_accept_kernel,  (const void*)block_mark_kernel,     (const void*)block_count_kernel,
+      (const void*)block_rank_kernel,     (const void*)zero_kernel,           (const void*)fold_kernel,
+      (const void*)prob_kernel,           (const void*)overlap_kernel,        (const void*)overlap_finish_kernel};
+  for (const void* k : ks) check(cudaFuncGetAttributes(&a, k), "cudaFuncGetAttributes (preload)");
+  (void)num_sms();
 }
 
 }  // namespace sf

@@ -86,9 +86,9 @@ struct GatherLaunch {
   const uint32_t* tabA;  // 8 x 256 byte tables: x byte -> layout index part
   const uint32_t* tabB;
   const uint64_t* bits;
-  double* acc;           // 2n doubles
+  double* acc;           // 2n doubles; every final's term is added to it in order
+  double* comp;          // null, or 2n compensation terms (SF_PREC_COMPENSATED)
   int64_t n;
-  int32_t accumulate;    // 0: acc = sum, 1: acc += sum
   int32_t g;             // deferred gates
   int32_t nterm_bits;    // log2 terms per deferred gate (1 or 2)
   GatherSide A, B;
@@ -243,16 +243,30 @@ uint64_t feistel(uint64_t v, int w, uint64_t key);
 struct ExecCtx {
   void** cache_slot = nullptr;
   bool profile = true;
+  const volatile int* cancel = nullptr;  // single-request form
+  int* err = nullptr;                    // error flag to use instead of the plan's
+  int64_t budget = 0;                    // memory budget instead of the plan's
+};
+// One request of a batch on one plan: its bitstrings, selection (ranges),
+// output and cancellation flag.
+struct ExecReq {
+  const uint64_t* d_bits = nullptr;
+  int64_t n = 0;
+  std::vector<Range> rs;
+  double* d_out = nullptr;
+  int accumulate = 0;
   const volatile int* cancel = nullptr;
-  // device tables, error flag and memory budget to use instead of the plan's
-  const uint32_t* tabA = nullptr;
-  const uint32_t* tabB = nullptr;
-  int* err = nullptr;
-  int64_t budget = 0;
+  bool cancelled = false;  // set by exec_run
 };
 size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget = 0);
+size_t exec_workspace_bytes(const Plan& p, const std::vector<ExecReq>& reqs, int64_t budget = 0);
 void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, double* d_out,
               int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
+              ExecCtx* ctx = nullptr);
+// The union of the requests' paths evolved once, each request gathered into
+// its own output; fails with SF_ECANCELLED only when every request is
+// cancelled (the others' results are then complete).
+void exec_run(Plan& p, std::vector<ExecReq>& reqs, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
               ExecCtx* ctx = nullptr);
 void exec_free_cache(void* cache);
 
@@ -261,6 +275,13 @@ void cost_terms(const Plan& p, const sf_path_sel& s, int64_t n_a, double t[4]);
 
 // Run-time specialised pass kernels (jit.cpp).
 void jit_prepare(Plan& p);
+void jit_load(Plan& p);  // load the plan's specialised kernels on the current device
+// The fixed scratch of sf_amplitudes_device_noalloc: its device address on
+// `device` (looked up once, with that device current).
+void* noalloc_prepare(int device);
+// Waits for the stream, reads and clears a wait-timeout flag; fails with
+// SF_ECUDA if it was set or a timeout was injected (sf_debug_inject_wait_timeouts).
+void check_wait_flag(int* d_flag, void* stream);
 std::string jit_source(const PassPlan& pp);
 void launch_pass_jit(const PassLaunch& L, int tiles, void* entry, void* stream);
 void ensure_device(Plan& p);
@@ -289,9 +310,15 @@ struct BlockMapLaunch {
   uint32_t* sums[2];
   uint32_t* count[2];
 };
-int launch_block_maps(const BlockMapLaunch& L, void* stream);  // returns kernels launched
+// Marks the parts of every set of bitstrings (L.bits / L.n are replaced by
+// each set in turn); returns kernels launched.
+int launch_block_maps(const BlockMapLaunch& L, const std::vector<std::pair<const uint64_t*, int64_t>>& sets,
+                      void* stream);
 void launch_zero(double* p, int64_t n_doubles, void* stream);
-void launch_overlap(const double* a, const double* b, int64_t n, double* out, void* stream);
+void launch_fold(double* out, const double* comp, int64_t n_doubles, void* stream);
+void launch_prob(const double* amps, int64_t n, double scale, double* probs, void* stream);
+void launch_overlap(const double* a, const double* b, int64_t n, double* out, void* stream);  // out: 5 doubles
+void preload_kernels();  // load every static kernel into the current context
 void launch_frugal(const double* amps, const double* u, int64_t n, double N, double mp, double scale,
                    uint8_t* acc, int64_t* count, void* stream);
 
@@ -306,9 +333,10 @@ struct SfHostBuffers {  // device buffers of the host-pointer call, reused
   void* ws = nullptr;
   size_t ws_bytes = 0;
   uint64_t* bits = nullptr;
-  double* out = nullptr;
+  double* out = nullptr;   // 3 cap_n doubles: amplitudes, then probabilities
   int64_t cap_n = 0;
   void* stream = nullptr;  // cudaStream_t
+  double* probs(int64_t n) { (void)n; return out + 2 * cap_n; }
 };
 
 struct sf_plan {

@@ -89,8 +89,10 @@ extern "C" int sf_plan_autotune(const sf_circuit* c, const sf_plan_opts* base, c
           if (P->d_tabA) cudaFree(P->d_tabA);
           if (P->d_tabB) cudaFree(P->d_tabB);
           if (P->d_err) cudaFree(P->d_err);
+          if (P->d_cnt) cudaFree(P->d_cnt);
           P->d_tabA = P->d_tabB = nullptr;
           P->d_err = nullptr;
+          P->d_cnt = nullptr;
           if (ms * 1e-3 < best_t) {
             best_t = ms * 1e-3;
             best_o = o;

@@ -20,6 +20,8 @@ SF_H, SF_X_HALF, SF_Y_HALF, SF_T, SF_Z, SF_S, SF_CZ, SF_ISWAP, SF_U1, SF_U2 = ra
 SF_DEC_SCHMIDT, SF_DEC_BLOCK4 = 0, 1
 SF_EXEC_BATCHED, SF_EXEC_PLAIN = 0, 1
 SF_SEL_RANGE, SF_SEL_FRACTION, SF_SEL_LIST = 0, 1, 2
+SF_PREC_F64, SF_PREC_COMPENSATED = 0, 1
+SF_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED = [
     "sf_circuit_create", "sf_circuit_parse", "sf_circuit_info", "sf_circuit_destroy",
@@ -30,6 +32,8 @@ EXPORTED = [
     "sf_plan_profile_read", "sf_amplitudes_device_noalloc", "sf_plan_segment_stats",
     "sf_plan_describe", "sf_frugal_accept_device", "sf_plan_autotune", "sf_overlap_device",
     "sf_plan_cost_terms", "sf_cost_fit", "sf_cost_predict", "sf_server_set_cost_model", "sf_last_error",
+    "sf_plan_status", "sf_debug_inject_wait_timeouts", "sf_probabilities", "sf_probabilities_device",
+    "sf_workspace_size_batch", "sf_amplitudes_device_batch", "sf_debug_set_wait_flag", "sf_server_stats",
 ]
 
 
@@ -51,13 +55,18 @@ class sf_plan_opts(ctypes.Structure):
                 ("defer_last_level", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("batch_paths", ctypes.c_int32), ("run_bits", ctypes.c_int32),
                 ("jit", ctypes.c_int32), ("split_last", ctypes.c_int32), ("fp32x2", ctypes.c_int32),
-                ("dense_finals", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("dense_finals", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sf_path_sel(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("first", ctypes.c_uint64), ("count", ctypes.c_uint64),
                 ("fidelity", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("list", ctypes.POINTER(ctypes.c_uint64)), ("n_list", ctypes.c_int64)]
+
+
+class sf_request(ctypes.Structure):
+    _fields_ = [("d_bitstrings", ctypes.c_void_p), ("n", ctypes.c_int64), ("sel", ctypes.POINTER(sf_path_sel)),
+                ("d_out_amps", ctypes.c_void_p), ("accumulate", ctypes.c_int32)]
 
 
 _lib = None
@@ -107,6 +116,14 @@ def lib():
             "sf_cost_predict": (ctypes.c_double, [P, P]),
             "sf_server_set_cost_model": (i32, [P, P, ctypes.c_double]),
             "sf_last_error": (ctypes.c_char_p, []),
+            "sf_plan_status": (i32, [P, P]),
+            "sf_debug_inject_wait_timeouts": (i32, [i32]),
+            "sf_probabilities": (i32, [P, P, i64, P, i32, P, P]),
+            "sf_probabilities_device": (i32, [P, i64, ctypes.c_double, P, P]),
+            "sf_workspace_size_batch": (i32, [P, P, i32, P]),
+            "sf_amplitudes_device_batch": (i32, [P, P, i32, P, ctypes.c_size_t, P]),
+            "sf_debug_set_wait_flag": (i32, [P, i32]),
+            "sf_server_stats": (i32, [P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -259,6 +276,74 @@ def sf_amplitudes_into(plan, bits_u64, sel, out_f64):
     return fa.value
 
 
+def sf_probabilities(plan, bitstrings, sel, divide_by_f=False):
+    """Host form: returns (float64 probabilities |amp|^2 [/ f_actual], f_actual)."""
+    bits = np.ascontiguousarray(bitstrings, dtype=np.uint64)
+    out = np.zeros(len(bits), dtype=np.float64)
+    fa = ctypes.c_double()
+    _check(lib().sf_probabilities(plan, _ptr(bits), len(bits), ctypes.byref(sel), 1 if divide_by_f else 0,
+                                  _ptr(out), ctypes.byref(fa)))
+    return out, fa.value
+
+
+def sf_probabilities_device(d_amps, d_probs, scale=1.0, stream=None):
+    """|amp|^2 * scale of float64 (n, 2) device amplitudes into float64 (n,)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().sf_probabilities_device(ctypes.c_void_p(d_amps.data_ptr()), d_probs.numel(), float(scale),
+                                         ctypes.c_void_p(d_probs.data_ptr()), ctypes.c_void_p(stream.cuda_stream)))
+
+
+def sf_plan_status(plan, stream=None):
+    """Waits for the stream; raises SFError(SF_ECUDA) if a kernel wait of this
+    plan timed out since the last check (and clears the flag)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().sf_plan_status(plan, ctypes.c_void_p(stream.cuda_stream)))
+
+
+def sf_debug_inject_wait_timeouts(count):
+    """Test hook: the next `count` wait-timeout checks report a timeout."""
+    _check(lib().sf_debug_inject_wait_timeouts(count))
+
+
+def sf_debug_set_wait_flag(plan, value=1):
+    """Test hook: write `value` into the plan's device wait-timeout flag."""
+    _check(lib().sf_debug_set_wait_flag(plan, value))
+
+
+def _requests(reqs):
+    """reqs: [(d_bits, sel, d_out, accumulate)] -> ctypes array (kept alive by the caller)."""
+    arr = (sf_request * max(1, len(reqs)))()
+    for i, (d_bits, sel, d_out, acc) in enumerate(reqs):
+        arr[i].d_bitstrings = d_bits.data_ptr()
+        arr[i].n = d_bits.numel()
+        arr[i].sel = ctypes.pointer(sel)
+        arr[i].d_out_amps = d_out.data_ptr()
+        arr[i].accumulate = 1 if acc else 0
+    return arr
+
+
+def sf_workspace_size_batch(plan, reqs) -> int:
+    arr = _requests(reqs)
+    b = ctypes.c_size_t()
+    _check(lib().sf_workspace_size_batch(plan, arr, len(reqs), ctypes.byref(b)))
+    return b.value
+
+
+def sf_amplitudes_device_batch(plan, reqs, workspace, stream=None):
+    """Several requests on one plan in one run: reqs = [(d_bits, sel, d_out,
+    accumulate)] of torch device tensors (d_out float64 (n, 2))."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    arr = _requests(reqs)
+    _check(lib().sf_amplitudes_device_batch(plan, arr, len(reqs), ctypes.c_void_p(workspace.data_ptr()),
+                                            workspace.numel(), ctypes.c_void_p(stream.cuda_stream)))
+
+
 def sf_workspace_size(plan, n, sel) -> int:
     b = ctypes.c_size_t()
     _check(lib().sf_workspace_size(plan, n, ctypes.byref(sel), ctypes.byref(b)))
@@ -320,6 +405,13 @@ def sf_server_times(server, ticket):
     return q.value, t.value
 
 
+def sf_server_stats(server):
+    """(batches, requests in them, largest batch) run by the server."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sf_server_stats(server, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 def sf_server_destroy(server):
     lib().sf_server_destroy(server)
 
@@ -349,7 +441,8 @@ def sf_frugal_accept_device(d_amps, d_uniform, n_qubits, mprime, d_accept, d_cou
 
 
 def sf_overlap_device(d_a, d_b, d_out, stream=None):
-    """<a|b>, <a|a>, <b|b> of two float64 (n, 2) device tensors into d_out (4,)."""
+    """<a|b> (re, im), <a|a>, <b|b> and the estimate f_e of two float64 (n, 2)
+    device tensors into d_out (5,)."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -358,10 +451,9 @@ def sf_overlap_device(d_a, d_b, d_out, stream=None):
                                    ctypes.c_void_p(stream.cuda_stream)))
 
 
-def fidelity_estimate(sums):
-    """f_e = |<a|b>|^2 / (<a|a><b|b>) from the four sums of sf_overlap_device."""
-    re, im, na, nb = [float(v) for v in sums]
-    return (re * re + im * im) / (na * nb)
+def fidelity_estimate(out):
+    """f_e as sf_overlap_device computed it (the fifth of its outputs)."""
+    return float(out[4])
 
 
 def sf_plan_cost_terms(plan, sel, n_a):

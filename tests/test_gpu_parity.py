@@ -1,11 +1,23 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
 Tolerance (the contract for complex64 halves with FP64 path accumulation):
-max |amp_gpu - amp_oracle| <= 1e-5 * 2^{-n/2}; sums over few paths are also
-held to 1e-4 of the RMS oracle amplitude, since their values are far below
-2^{-n/2} (complex64 evolution through ~600 gates per half leaves ~1e-5 of
-the typical amplitude).
+max |amp_gpu - amp_oracle| <= 1e-5 * 2^{-n/2}. A sum over few paths is far
+below 2^{-n/2} (at n = 56 one path is ~2^{-45.5}), where that bound says
+nothing, so every case is also held to a relative bound:
+    max |d| <= REL_TOL * s,   s = sqrt(mean_x sum_j |a_j(x)|^2),
+the magnitude of a sum of paths with independent phases (the RMS of the
+summed amplitude when the paths' phases are random), computed from the
+oracle's per-path amplitudes a_j where the test has them, else the RMS of
+the oracle's sum. Error model: each path's two halves are evolved in FP32
+through G gate applications each (G ~ 300 at 6x7, ~560 at 7x8 on the
+B half), every one adding a relative rounding of order 2^-24 with a random
+sign, so a path's relative error is ~ sqrt(2G) 2^-24 ~ 2e-6 at 7x8; independent
+errors over paths add like the paths themselves, which is what s scales.
+REL_TOL = 3e-5 leaves a factor of ~15 over that estimate; the measured
+values (printed per case) are recorded beside the bound in the design notes.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -17,7 +29,8 @@ from paper_1807_10749_gb300 import inputs, sfsim
 pytestmark = pytest.mark.gpu
 
 ABS_TOL = 1e-5
-REL_TOL = 1e-4
+REL_TOL = 3e-5
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,16 +57,25 @@ def jit(request, monkeypatch):
     return request.param
 
 
-def check_close(gpu, ref, n, label="", nonzero=True):
+def check_close(gpu, ref, n, label="", nonzero=True, path_scale=None):
+    """path_scale: s of the module docstring from per-path oracle values
+    (None: the RMS of the oracle's sum)."""
     err = np.abs(gpu - ref)
     rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    s = rms if path_scale is None else path_scale
     if nonzero:
         assert rms > 0, f"{label}: the reference is identically zero (vacuous comparison)"
     bound = ABS_TOL * 2.0 ** (-n / 2)
     print(f"{label}: max|d| = {err.max():.3e} (= {err.max() / 2.0 ** (-n / 2):.2e} * 2^-n/2), "
-          f"rms|ref| = {rms:.3e}, rms|d| = {np.sqrt(np.mean(err ** 2)):.3e}")
+          f"max|d|/s = {err.max() / s:.2e}, rms|d|/s = {np.sqrt(np.mean(err ** 2)) / s:.2e}, "
+          f"rms|ref| = {rms:.3e}, s = {s:.3e}")
     assert err.max() <= bound, f"{label}: {err.max()} > {bound}"
-    assert err.max() <= REL_TOL * rms + 1e-300, f"{label}: {err.max()} > {REL_TOL} * rms {rms}"
+    assert err.max() <= REL_TOL * s + 1e-300, f"{label}: {err.max()} > {REL_TOL} * s {s}"
+
+
+def path_scale(per_path):
+    """s = sqrt(mean_x sum_j |a_j(x)|^2) from per-path amplitudes (paths x bitstrings)."""
+    return float(np.sqrt(np.mean(np.sum(np.abs(per_path) ** 2, axis=0))))
 
 
 _REF_CACHE = {}
@@ -64,6 +86,15 @@ def oracle_sf(setup_key, setup, ids, bits):
     key = (setup_key, np.asarray(ids, dtype=np.uint64).tobytes(), bits.tobytes())
     if key not in _REF_CACHE:
         _REF_CACHE[key] = sim.sf_amplitudes(setup, ids, bits)
+    return _REF_CACHE[key]
+
+
+def oracle_per_path(setup_key, setup, ids, bits):
+    """The oracle's amplitudes of each path alone (paths x bitstrings), once
+    per case for all kernel forms."""
+    key = ("per-path", setup_key, np.asarray(ids, dtype=np.uint64).tobytes(), bits.tobytes())
+    if key not in _REF_CACHE:
+        _REF_CACHE[key] = np.stack([sim.sf_amplitudes(setup, np.array([j], dtype=np.uint64), bits) for j in ids])
     return _REF_CACHE[key]
 
 
@@ -227,39 +258,66 @@ def test_5x6_full_sum_porter_thomas(jit):
 # ---------------------------------------------------------------- 6x7 (C3)
 @pytest.mark.parametrize("kind,split", [("cz", 0), ("cz", 1), ("haar", 0)])
 def test_6x7_path_list_matches_oracle(kind, split, jit):
+    """64 paths x 4096 bitstrings. CZ: 48 random paths and one whole group of
+    the folded last level (16 leaves, contracted in closed form). Haar (every
+    cut gate branches 4 ways): 32 random paths and 32 leaves of one group of
+    256 (the partial-group form of the contraction)."""
     w, text = workload("6x7_d26", haar=(kind == "haar"))
     c = ocirc.parse(text)
     setup = sim.SFSetup(c, w["side_b_mask"])
     bits = inputs.random_bitstrings(42, 4096, w["bitstring_seed"])
-    ids = inputs.random_path_list(setup.x_bits, 12 if kind == "cz" else 6, 11)
-    # include a whole last-level group so the deferred contraction is used
+    ids = inputs.random_path_list(setup.x_bits, 48 if kind == "cz" else 32, 11)
     grp = (int(ids[0]) >> 4) << 4 if kind == "cz" else (int(ids[0]) >> 8) << 8
-    full = np.arange(grp, grp + (16 if kind == "cz" else 256), dtype=np.uint64)
+    full = np.arange(grp, grp + (16 if kind == "cz" else 32), dtype=np.uint64)
     ids = np.unique(np.concatenate([ids, full]))
-    if kind == "haar":
-        ids = np.unique(np.concatenate([ids[:6], full[:40]]))
-    ref = oracle_sf(("6x7", kind), setup, ids, bits)
+    per = oracle_per_path(("6x7", kind), setup, ids, bits)
+    ref = per.sum(axis=0)
     # split = 0: the level before the folded last level runs inside the last
     # program; split = 1: as its own segment with the node in between
     p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], split_last=split)
     amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
-    check_close(amp, ref, 42, f"6x7 {kind} split={split} {len(ids)} paths")
+    check_close(amp, ref, 42, f"6x7 {kind} split={split} {len(ids)} paths", path_scale=path_scale(per))
     p.close()
 
 
 # ---------------------------------------------------------------- 7x8 (C4)
+def test_7x8_paths_match_stored_oracle(jit):
+    """Full size (28+28 qubits, 2 GiB halves) at the benchmark's density:
+    the plan runs all 1M bitstrings of the workload (compact final passes,
+    as in the benchmark), and the first 1024 are compared with the FP64
+    oracle's per-path amplitudes stored by tests/golden/make_oracle_7x8.py:
+    24 paths of the first selected prefix (f = 0.5%, seed 7) - one whole
+    16-leaf group of the folded last level and 8 paths of other groups."""
+    w, text = workload("7x8_d40")
+    g = np.load(os.path.join(GOLDEN, "oracle_7x8_d40_paths.npz"))
+    ids, amps = g["ids"], g["amps"]
+    bits = inputs.random_bitstrings(56, w["n_bitstrings"], w["bitstring_seed"])
+    assert np.array_equal(bits[:len(g["bits"])], g["bits"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
+    sel_all = sfsim.selection("list", ids=ids)
+    assert sfsim.sf_workspace_size(p.handle, len(bits), sel_all) > \
+        sfsim.sf_workspace_size(p.handle, 1024, sel_all), "compact finals not sized for 1M bitstrings"
+    assert np.all(ids[:16] >> 4 == ids[0] >> 4) and ids[0] % 16 == 0
+    for label, rows in [("whole 16-leaf group", slice(0, 16)), ("8 paths of other groups", slice(16, 24)),
+                        ("all 24 paths", slice(0, 24))]:
+        amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids[rows]))
+        per = amps[rows]
+        check_close(amp[:per.shape[1]], per.sum(axis=0), 56, f"7x8 {label}", path_scale=path_scale(per))
+    p.close()
+
+
 def test_7x8_path_list_matches_oracle(jit):
-    """Full size (28+28 qubits, 2 GiB halves): a seeded path list x 1024
-    bitstrings against the oracle (v2 circuit: every path is non-zero)."""
+    """A seeded path list x 1024 bitstrings against the oracle run here (v2
+    circuit: every path is non-zero)."""
     w, text = workload("7x8_d40")
     c = ocirc.parse(text)
     setup = sim.SFSetup(c, w["side_b_mask"])
     bits = inputs.random_bitstrings(56, 1024, w["bitstring_seed"])
     ids = inputs.random_path_list(setup.x_bits, 2, 8)
-    ref = oracle_sf(("7x8",), setup, ids, bits)
+    per = oracle_per_path(("7x8",), setup, ids, bits)
     p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"])
     amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
-    check_close(amp, ref, 56, "7x8 2 paths")
+    check_close(amp, per.sum(axis=0), 56, "7x8 2 random paths", path_scale=path_scale(per))
     p.close()
 
 

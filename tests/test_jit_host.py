@@ -3,7 +3,7 @@ packed FP32x2 forms of each specialised pass are compiled with g++ against
 small stand-ins for the CUDA types and intrinsics they use, every stage
 thread runs as a host thread (the stage barrier as a std::barrier) over the
 same random tile, and the two forms must give the same tile. This covers the
-packed code generation, which the default plans do not use."""
+packed code generation on every kind of stage the benchmark plans hold."""
 import os
 import re
 import shutil
@@ -102,9 +102,23 @@ int main() {
 '''.replace("NTHREADS", str(nthreads)).replace("NTILE", str(ntile))
 
 
+def _compile_run(tmp_path, tag, scalar, packed, nt):
+    cpp = tmp_path / f"{tag}.cpp"
+    cpp.write_text(_harness(scalar, packed, nt, 1 << 13))
+    exe = tmp_path / f"{tag}.bin"
+    r = subprocess.run(["g++", "-std=c++20", "-O1", "-ffp-contract=off", "-I", CSRC, str(cpp), "-o", str(exe),
+                        "-pthread"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[:3000]
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    md, mx = map(float, out.stdout.split())
+    return md, mx
+
+
 @pytest.mark.skipif(shutil.which("g++") is None, reason="g++ not available")
-@pytest.mark.parametrize("name", ["4x4_d10", "5x6_d24"])
-def test_packed_and_scalar_stage_programs_agree(name, tmp_path):
+@pytest.mark.parametrize("name,stride", [("4x4_d10", 1), ("5x6_d24", 1), ("6x7_d26", 3), ("7x8_d40", 4)])
+def test_packed_and_scalar_stage_programs_agree(name, stride, tmp_path):
+    """Every stride-th pass of the plan (all three forms of a stage: packed
+    butterflies, odd phases, per-thread signs and phases, post scales)."""
     w = inputs.WORKLOADS[name]
     text = inputs.workload_circuit(name).text()
     dirs = {}
@@ -122,22 +136,36 @@ def test_packed_and_scalar_stage_programs_agree(name, tmp_path):
             del os.environ["SF_JIT_DUMP"]
         plan.close()
         dirs[packed] = d
-    files = sorted(os.listdir(dirs[1]))
+    files = sorted(os.listdir(dirs[1]), key=lambda f: int(f.split("_")[1].split(".")[0]))
     assert files
     n_packed = 0
-    for f in files[:4]:
+    for f in files[::stride][:12]:
         scalar, nt = _extract(os.path.join(dirs[0], f))
         packed, nt2 = _extract(os.path.join(dirs[1], f))
         assert nt == nt2
         n_packed += packed.count("(packed)")
-        cpp = tmp_path / f"{f}.cpp"
-        cpp.write_text(_harness(scalar, packed, nt, 1 << 13))
-        exe = tmp_path / f"{f}.bin"
-        r = subprocess.run(["g++", "-std=c++20", "-O1", "-ffp-contract=off", "-I", CSRC, str(cpp), "-o", str(exe),
-                            "-pthread"], capture_output=True, text=True)
-        assert r.returncode == 0, r.stderr[:3000]
-        out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
-        md, mx = map(float, out.stdout.split())
+        md, mx = _compile_run(tmp_path, f, scalar, packed, nt)
         assert mx > 0
         assert md <= 1e-5 * mx, (f, md, mx)
     assert n_packed > 0   # the check exercised packed stages
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="g++ not available")
+def test_harness_catches_a_planted_mistake(tmp_path):
+    """A sign flipped in one packed butterfly of a 5x6 pass must show up."""
+    w = inputs.WORKLOADS["5x6_d24"]
+    text = inputs.workload_circuit("5x6_d24").text()
+    srcs = []
+    for packed in (0, 1):
+        d = tmp_path / f"p{packed}"
+        d.mkdir()
+        os.environ["SF_JIT_DUMP"] = str(d)
+        try:
+            sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=1, fp32x2=packed).close()
+        finally:
+            del os.environ["SF_JIT_DUMP"]
+        srcs.append(_extract(os.path.join(d, "pass_2.cu")))
+    (scalar, nt), (packed, _) = srcs
+    assert "__fadd2_rn(a, b)" in packed
+    md, mx = _compile_run(tmp_path, "planted", scalar, packed.replace("__fadd2_rn(a, b)", "__fadd2_rn(b, b)", 1), nt)
+    assert md > 1e-3 * mx

@@ -126,3 +126,28 @@ def test_failed_request_does_not_affect_others(plans):
         assert np.array_equal(sfsim.sf_server_wait(srv, t, len(bits)), plan.amplitudes(bits, sel)[0])
     finally:
         sfsim.sf_server_destroy(srv)
+
+
+def test_queued_requests_on_one_plan_run_as_one_batch(plans):
+    """Requests that queue up on one plan while the only worker is busy run
+    together as one batch (one path tree, every pass launch carrying all of
+    them); each result is bit for bit the request's result alone."""
+    long_plan, n_long = plans["long"]
+    plan, n = plans["5x6"]
+    reqs = [(inputs.random_bitstrings(n, 300 + 100 * i, 70 + i),
+             sfsim.selection("fraction", fidelity=[1.0, 0.25, 0.5, 1 / 16, 1.0][i], seed=3 + i)) for i in range(5)]
+    alone = [plan.amplitudes(b, s)[0] for b, s in reqs]
+    srv = sfsim.sf_server_create(0, 1)
+    try:
+        b_long = inputs.random_bitstrings(n_long, 500, 9)
+        t0 = sfsim.sf_server_submit(srv, long_plan.handle, b_long, sfsim.selection("fraction", fidelity=1 / 32))
+        time.sleep(0.2)   # the long request occupies the worker
+        tickets = [sfsim.sf_server_submit(srv, plan.handle, b, s) for b, s in reqs]
+        sfsim.sf_server_wait(srv, t0, len(b_long))
+        for t, (b, s), a in zip(tickets, reqs, alone):
+            assert np.array_equal(sfsim.sf_server_wait(srv, t, len(b)), a)
+        batches, requests, largest = sfsim.sf_server_stats(srv)
+        print("server batches", batches, "requests", requests, "largest", largest)
+        assert requests == 6 and largest == 5 and batches == 2
+    finally:
+        sfsim.sf_server_destroy(srv)

@@ -22,7 +22,7 @@ def _overlap(a, b):
     import torch
     da = torch.from_numpy(np.stack([a.real, a.imag], 1).copy()).cuda()
     db = torch.from_numpy(np.stack([b.real, b.imag], 1).copy()).cuda()
-    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
     sfsim.sf_overlap_device(da, db, out)
     torch.cuda.synchronize()
     return out.cpu().numpy()
@@ -33,10 +33,14 @@ def test_overlap_sums_match_oracle(n):
     rng = np.random.default_rng(n + 1)
     a = rng.normal(size=n) + 1j * rng.normal(size=n)
     b = rng.normal(size=n) + 1j * rng.normal(size=n)
-    got = _overlap(a, b)
+    out = _overlap(a, b)
+    got = out[:4]
     want = np.array(validation.overlap_sums(a, b)) if n else np.zeros(4)
     # FP64 sums in another order: relative rounding ~ n * 2^-53
     assert np.all(np.abs(got - want) <= 1e-12 * (np.abs(a).sum() * np.abs(b).sum() / max(n, 1) + n))
+    # the library's estimate f_e (Appendix C), 0 for empty sets
+    fe = validation.fidelity_estimate(a, b) if n else 0.0
+    assert abs(out[4] - fe) <= 1e-10 * max(fe, 1e-300) + 1e-15
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +67,7 @@ def test_fidelity_estimate_tracks_f_actual(c2, f):
     for seed in (5, 6, 7):
         ver, f_actual = plan.amplitudes(bits, sfsim.selection("fraction", fidelity=f, seed=seed))
         sums = _overlap(exact, ver)
-        np.testing.assert_allclose(sums, validation.overlap_sums(exact, ver), rtol=1e-10)
+        np.testing.assert_allclose(sums[:4], validation.overlap_sums(exact, ver), rtol=1e-10)
         fe = sfsim.fidelity_estimate(sums)
         f1 = 2.0 ** 30 * np.mean(np.abs(ver) ** 2)
         print(f"f = {f}, seed {seed}: f_e = {fe:.4f}, f1 = {f1:.4f}, f_actual = {f_actual:.4f}")
