@@ -117,11 +117,11 @@ typedef struct {
                                the level before it and the last segment as one
                                program (no node is written between them), 1 = two
                                programs with the node in between */
-  int32_t fp32x2;           /* specialised kernels: 1 = register stages made only of
-                               H, X^1/2, Y^1/2 and phase groups keep each complex
-                               amplitude in one FP32x2 register pair, so a
-                               butterfly is one packed add per output; 0 = scalar
-                               FP32 arithmetic */
+  int32_t fp32x2;           /* specialised kernels: 1 (default) = register stages
+                               made only of H, X^1/2, Y^1/2 and phase groups keep
+                               each complex amplitude in one FP32x2 register pair,
+                               so a butterfly is one packed add per output; 0 =
+                               scalar FP32 arithmetic */
   int32_t dense_finals;     /* with the last level folded into the gather: 0 = the
                                last pass of each half's final program writes only
                                the blocks of 2^g amplitudes (g = cut gates of the
@@ -198,16 +198,23 @@ typedef struct {
   int64_t n_list;
 } sf_path_sel;
 
-/* Autotuner: plans the circuit with every candidate (tile_bits in {11, 12, 13},
- * fuse_bits in {4, 5}, run_bits in {3, 4, 5}) on top of *base (with base->jit
- * set, each candidate's specialised kernels are compiled first), runs the first
- * sample_paths paths of *sel for the n device bitstrings d_bits once to warm
- * up and once timed (CUDA events, a private stream), and writes the fastest
- * candidate's options to *best and its time to *best_seconds (may be NULL).
+/* Autotuner (batching axis): times candidate plans of the circuit on the
+ * first sample_paths paths of *sel (as a path list) for the n device
+ * bitstrings d_bits - once to warm up, once timed with CUDA events on a
+ * private stream - and writes the fastest candidate's options to *best, its
+ * time to *best_seconds and the time of *base itself to *base_seconds (either
+ * may be NULL). *base is always a candidate, so *best_seconds <= *base_seconds.
+ * Stage 1 searches the pass shape on top of *base: tile_bits 0 (the planner's
+ * per-segment choice, with run_bits 0), 12 or 13 with run_bits 3 or 4, each with
+ * fusion width fuse_bits = k in {2, 3, 4, 5} register qubits per thread block
+ * (k = 6 would need 64 amplitudes per thread: more registers than a thread of
+ * the pass kernel holds). Stage 2 varies batch_paths, the leaf groups per
+ * launch, over {1, 4, 16, 64, 256, 1024} at the best shape. With base->jit set
+ * each candidate's specialised kernels are compiled before it is timed.
  * Allocates and frees the device memory it needs. */
 SF_API int sf_plan_autotune(const sf_circuit* c, const sf_plan_opts* base, const sf_path_sel* sel,
                             int64_t sample_paths, const uint64_t* d_bits, int64_t n, sf_plan_opts* best,
-                            double* best_seconds);
+                            double* best_seconds, double* base_seconds);
 
 /* Runtime model of Section 8 (Eq. t_tot), with a fixed cost per request:
  *   T = C0 + C1 f 2^{x_p} (q1 2^{q1} + q2 2^{q2}) (d_p + C2 2^{x_b} d_b) + C3 P n_a
@@ -254,7 +261,13 @@ SF_API int sf_workspace_size(const sf_plan* p, int64_t n, const sf_path_sel* sel
  * and the result is valid once the stream reaches it. With accumulate != 0 the
  * sums are added to d_out_amps; otherwise d_out_amps is overwritten. Check
  * sf_plan_status once the stream is done: a kernel whose bounded wait gave
- * up leaves the result invalid. */
+ * up leaves the result invalid.
+ * Resident nodes: the plan leaves path-tree nodes in the workspace, and its
+ * next call with the same workspace reuses those it needs (the path prefixes
+ * that consecutive selections share, Section 2's checkpoints). The library
+ * records which plan ran last in each workspace and reuses nothing after
+ * another plan ran there; a caller that writes the workspace memory itself
+ * between two calls of one plan must call sf_plan_drop_resident first. */
 SF_API int sf_amplitudes_device(sf_plan* p, const uint64_t* d_bitstrings, int64_t n, const sf_path_sel* sel,
                          double* d_out_amps, int accumulate, void* d_workspace, size_t ws_bytes,
                          void* cuda_stream);
@@ -285,6 +298,10 @@ SF_API int sf_amplitudes_device_batch(sf_plan* p, const sf_request* reqs, int n_
  * forms (sf_amplitudes, sf_probabilities) and the server check the flag
  * themselves and return SF_ECUDA for the call or request concerned. */
 SF_API int sf_plan_status(sf_plan* p, void* cuda_stream);
+
+/* Forget the plan's resident nodes (its next device call recomputes every
+ * node) and free the device buffers its host-form calls keep. */
+SF_API int sf_plan_drop_resident(sf_plan* p);
 
 /* Test hook (host side, nothing is run on the device): the next `count`
  * checks of a wait-timeout flag, in any form, report a timeout as if a

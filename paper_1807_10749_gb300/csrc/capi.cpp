@@ -166,6 +166,7 @@ void sf_plan_opts_default(sf_plan_opts* o) {
   o->exec_mode = SF_EXEC_BATCHED;
   o->defer_last_level = 1;
   o->jit = 1;
+  o->fp32x2 = 1;
   o->precision = SF_PREC_F64;
 }
 
@@ -276,7 +277,10 @@ int sf_plan_describe(const sf_plan* h, char* buf, size_t cap, size_t* len) {
 }
 
 static void free_host_buffers(HostBuffers& hb) {
-  if (hb.ws) cudaFree(hb.ws);
+  if (hb.ws) {
+    sf::exec_forget_workspace(hb.ws);
+    cudaFree(hb.ws);
+  }
   if (hb.bits) cudaFree(hb.bits);
   if (hb.out) cudaFree(hb.out);
   if (hb.stream) cudaStreamDestroy((cudaStream_t)hb.stream);
@@ -414,6 +418,15 @@ int sf_amplitudes_device_batch(sf_plan* h, const sf_request* reqs, int n_req, vo
   SF_GUARD_END
 }
 
+int sf_plan_drop_resident(sf_plan* h) {
+  SF_GUARD_BEGIN
+  if (!h) sf::fail(SF_EINVAL, "null plan");
+  sf::exec_release_cache(*h->p);
+  free_host_buffers(h->hb);
+  return SF_OK;
+  SF_GUARD_END
+}
+
 int sf_plan_status(sf_plan* h, void* stream) {
   SF_GUARD_BEGIN
   if (!h) sf::fail(SF_EINVAL, "null plan");
@@ -488,7 +501,10 @@ static int host_form(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_
   }
   cudaStream_t hst = (cudaStream_t)hb.stream;
   if (hb.ws_bytes < need) {
-    if (hb.ws) cudaFree(hb.ws);
+    if (hb.ws) {
+      sf::exec_forget_workspace(hb.ws);
+      cudaFree(hb.ws);
+    }
     hb.ws = nullptr;
     hb.ws_bytes = 0;
     cuda_check(cudaMalloc(&hb.ws, need), "cudaMalloc workspace");

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <unordered_map>
 
 #include "sf_internal.h"
@@ -477,6 +478,19 @@ void prof_release(Plan& p) {
   p.prof.pool.clear();
 }
 
+namespace {
+// The last cache (identified by its slot) that ran in each workspace: a
+// cache may reuse the nodes it left in a workspace only if no other plan or
+// caller context ran there since.
+std::mutex g_ws_mu;
+std::unordered_map<const void*, const void*> g_ws_owner;
+}  // namespace
+
+void exec_forget_workspace(const void* ws) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  g_ws_owner.erase(ws);
+}
+
 void exec_release_cache(Plan& p) {
   delete reinterpret_cast<Cache*>(p.cache);
   p.cache = nullptr;
@@ -533,7 +547,15 @@ void exec_run(Plan& plan, std::vector<ExecReq>& reqs, void* ws, size_t ws_bytes,
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~(uintptr_t)255);
 
   Cache* C = reinterpret_cast<Cache*>(*cache_slot);
-  if (!C || !keep_cache || C->ws != ws || C->ws_bytes != ws_bytes || C->B != lay.B || C->cap != lay.cap) {
+  bool same_owner;
+  {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    auto it = g_ws_owner.find(ws);
+    same_owner = it != g_ws_owner.end() && it->second == (const void*)cache_slot;
+    g_ws_owner[ws] = (const void*)cache_slot;
+  }
+  if (!C || !keep_cache || !same_owner || C->ws != ws || C->ws_bytes != ws_bytes || C->B != lay.B ||
+      C->cap != lay.cap) {
     delete C;
     C = new Cache();
     *cache_slot = C;

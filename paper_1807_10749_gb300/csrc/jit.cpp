@@ -666,6 +666,7 @@ std::string layout_asserts() {
 
 // -------------------------------------------------------- compiled cache
 struct Entry {
+  std::string name;  // the kernel's name
   std::string src;
   std::string cubin;
   std::string err;
@@ -682,7 +683,11 @@ std::map<std::string, std::unique_ptr<Entry>>& cache() {
   return c;
 }
 
+// Kernel names: the last pass of a final program (the one that writes the
+// gather's input, compact or whole) is sf_pass_final, every other pass
+// sf_pass_spec, so profiles can tell them apart.
 const char* kKernelName = "sf_pass_spec";
+const char* kFinalKernelName = "sf_pass_final";
 
 void compile_entry(Entry* e) {
   const Nvrtc& n = nvrtc();
@@ -729,19 +734,30 @@ void jit_prepare(Plan& p) {
   const Nvrtc& n = nvrtc();
   if (!n.ok) fail(SF_EUNSUPPORTED, "run-time specialised kernels need NVRTC: " + n.why);
   std::vector<PassPlan*> all;
+  std::vector<bool> fin;
+  const size_t nL = p.levels.size();
   for (HalfPlan* h : {&p.A, &p.B}) {
-    for (auto& s : h->seg)
-      for (auto& pp : s.passes) all.push_back(&pp);
-    for (auto& pp : h->last_deferred.passes) all.push_back(&pp);
-    for (auto& pp : h->last_merged.passes) all.push_back(&pp);
+    // the final program: the merged or deferred last segment, else the last
+    SegmentPlan* last = p.merged_last ? &h->last_merged : (p.deferred ? &h->last_deferred : &h->seg[nL]);
+    auto add = [&](SegmentPlan& s) {
+      for (size_t i = 0; i < s.passes.size(); i++) {
+        all.push_back(&s.passes[i]);
+        fin.push_back(&s == last && i + 1 == s.passes.size());
+      }
+    };
+    for (auto& s : h->seg) add(s);
+    add(h->last_deferred);
+    add(h->last_merged);
   }
   std::vector<Entry*> todo;
   p.jit_entries.clear();
   const char* dump = std::getenv("SF_JIT_DUMP");  // directory for the generated sources
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    for (PassPlan* pp : all) {
-      std::string src = gen_pass(*pp, kKernelName, p.opts.fp32x2 != 0);
+    for (size_t ai = 0; ai < all.size(); ai++) {
+      PassPlan* pp = all[ai];
+      const char* kname = fin[ai] ? kFinalKernelName : kKernelName;
+      std::string src = gen_pass(*pp, kname, p.opts.fp32x2 != 0);
       if (dump) {
         const std::string fn = std::string(dump) + "/pass_" + std::to_string(p.jit_entries.size()) + ".cu";
         if (FILE* f = std::fopen(fn.c_str(), "w")) {
@@ -752,6 +768,7 @@ void jit_prepare(Plan& p) {
       auto& slot = cache()[src];
       if (!slot) {
         slot = std::make_unique<Entry>();
+        slot->name = kname;
         slot->src = src;
         todo.push_back(slot.get());
       }
@@ -805,7 +822,7 @@ void ready_entry(Entry* e, int threads, size_t smem) {
   if (!e->kern) {
     cudaError_t rc = cudaLibraryLoadData(&e->lib, e->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryLoadData: ") + cudaGetErrorString(rc));
-    rc = cudaLibraryGetKernel(&e->kern, e->lib, kKernelName);
+    rc = cudaLibraryGetKernel(&e->kern, e->lib, e->name.c_str());
     if (rc != cudaSuccess) fail(SF_ECUDA, std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(rc));
   }
   if (smem > e->smem_set) {

@@ -195,7 +195,10 @@ void extend_batch(sf_server& s, std::vector<std::shared_ptr<Request>>& b, int64_
 }
 
 void release_pool(Pool& p) {
-  if (p.ws) cudaFree(p.ws);
+  if (p.ws) {
+    sf::exec_forget_workspace(p.ws);
+    cudaFree(p.ws);
+  }
   if (p.bits) cudaFree(p.bits);
   if (p.out) cudaFree(p.out);
   p = Pool();
@@ -213,7 +216,10 @@ void run_batch(sf_server& s, std::vector<std::shared_ptr<Request>>& b, size_t ws
   try {
     cuda_ok(cudaSetDevice(s.device), "cudaSetDevice");
     if (pool.ws_bytes < ws_need) {
-      if (pool.ws) cudaFree(pool.ws);
+      if (pool.ws) {
+        sf::exec_forget_workspace(pool.ws);
+        cudaFree(pool.ws);
+      }
       pool.ws = nullptr;
       pool.ws_bytes = 0;
       cuda_ok(cudaMalloc(&pool.ws, ws_need), "cudaMalloc workspace");

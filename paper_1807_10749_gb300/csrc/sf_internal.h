@@ -269,6 +269,7 @@ void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, 
 void exec_run(Plan& p, std::vector<ExecReq>& reqs, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
               ExecCtx* ctx = nullptr);
 void exec_free_cache(void* cache);
+void exec_forget_workspace(const void* ws);  // no cache may reuse nodes left in ws
 
 // Features of the runtime model (Section 8, Eq. t_tot) for a request.
 void cost_terms(const Plan& p, const sf_path_sel& s, int64_t n_a, double t[4]);

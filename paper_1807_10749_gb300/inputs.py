@@ -266,6 +266,10 @@ WORKLOADS = {
     # larger than L2) in a few GB of device memory
     "5x10_d16": dict(rows=5, cols=10, depth=16, side_b_mask=column_cut_mask(5, 10, 5),
                      n_bitstrings=100_000, bitstring_seed=1005, v2=True),
+    # profiling case whose last branching level (2 cut CZs) folds into the
+    # gather, so its final passes write compact blocks at 1M bitstrings
+    "5x10_d14": dict(rows=5, cols=10, depth=14, side_b_mask=column_cut_mask(5, 10, 5),
+                     n_bitstrings=1_000_000, bitstring_seed=1006, v2=True),
 }
 
 

@@ -34,6 +34,7 @@ EXPORTED = [
     "sf_plan_cost_terms", "sf_cost_fit", "sf_cost_predict", "sf_server_set_cost_model", "sf_last_error",
     "sf_plan_status", "sf_debug_inject_wait_timeouts", "sf_probabilities", "sf_probabilities_device",
     "sf_workspace_size_batch", "sf_amplitudes_device_batch", "sf_debug_set_wait_flag", "sf_server_stats",
+    "sf_plan_drop_resident",
 ]
 
 
@@ -109,7 +110,7 @@ def lib():
             "sf_plan_describe": (i32, [P, P, ctypes.c_size_t, P]),
             "sf_frugal_accept_device": (i32, [P, P, i64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               P, P, P]),
-            "sf_plan_autotune": (i32, [P, P, P, i64, P, i64, P, P]),
+            "sf_plan_autotune": (i32, [P, P, P, i64, P, i64, P, P, P]),
             "sf_overlap_device": (i32, [P, P, i64, P, P]),
             "sf_plan_cost_terms": (i32, [P, P, i64, P]),
             "sf_cost_fit": (i32, [P, P, i64, P]),
@@ -124,6 +125,7 @@ def lib():
             "sf_amplitudes_device_batch": (i32, [P, P, i32, P, ctypes.c_size_t, P]),
             "sf_debug_set_wait_flag": (i32, [P, i32]),
             "sf_server_stats": (i32, [P, P, P, P]),
+            "sf_plan_drop_resident": (i32, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -211,14 +213,14 @@ def sf_plan_describe(plan) -> str:
 
 
 def sf_plan_autotune(circuit, base: sf_plan_opts, sel, sample_paths, d_bits):
-    """Fastest (tile_bits, fuse_bits, run_bits) for this circuit and request
-    sample, timed on the device: returns (sf_plan_opts, seconds)."""
+    """Fastest options for this circuit and request sample, timed on the
+    device: returns (sf_plan_opts, its seconds, the base options' seconds)."""
     best = sf_plan_opts()
-    t = ctypes.c_double()
+    t, t0 = ctypes.c_double(), ctypes.c_double()
     _check(lib().sf_plan_autotune(circuit, ctypes.byref(base), ctypes.byref(sel), sample_paths,
                                   ctypes.c_void_p(d_bits.data_ptr()), d_bits.numel(), ctypes.byref(best),
-                                  ctypes.byref(t)))
-    return best, t.value
+                                  ctypes.byref(t), ctypes.byref(t0)))
+    return best, t.value, t0.value
 
 
 def sf_plan_destroy(plan):
@@ -307,6 +309,11 @@ def sf_plan_status(plan, stream=None):
 def sf_debug_inject_wait_timeouts(count):
     """Test hook: the next `count` wait-timeout checks report a timeout."""
     _check(lib().sf_debug_inject_wait_timeouts(count))
+
+
+def sf_plan_drop_resident(plan):
+    """Forget resident nodes and free the host-form device buffers."""
+    _check(lib().sf_plan_drop_resident(plan))
 
 
 def sf_debug_set_wait_flag(plan, value=1):

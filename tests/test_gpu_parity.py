@@ -42,19 +42,19 @@ def built():
     sim.build()
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["generic", "specialised", "specialised-fp32x2"])
+@pytest.fixture(params=[0, 1, 2], ids=["generic", "specialised-scalar", "specialised-packed"])
 def jit(request, monkeypatch):
-    """The pass-kernel forms: the generic kernel, the per-pass specialised
-    kernels compiled at plan time, and those with packed FP32x2 stages."""
-    if request.param == 2:
+    """The pass-kernel forms: the generic kernel, and the per-pass specialised
+    kernels compiled at plan time with scalar FP32 stages or with packed
+    FP32x2 stages (the default)."""
+    if request.param == 1:
         orig = sfsim.Plan.__init__
 
-        def packed(self, text, **kw):
-            kw["fp32x2"] = 1
+        def scalar(self, text, **kw):
+            kw["fp32x2"] = 0
             orig(self, text, **kw)
-        monkeypatch.setattr(sfsim.Plan, "__init__", packed)
-        return 1
-    return request.param
+        monkeypatch.setattr(sfsim.Plan, "__init__", scalar)
+    return 0 if request.param == 0 else 1
 
 
 def check_close(gpu, ref, n, label="", nonzero=True, path_scale=None):

@@ -47,10 +47,11 @@ def _extract(path):
     """The stage program (the run function) of a dumped pass source as a
     struct of its own, and the number of stage threads."""
     src = open(path).read()
-    a = src.index("struct sf_pass_spec_prog {")
+    name = re.search(r"struct (sf_pass_\w+)_prog \{", src).group(1)
+    a = src.index(f"struct {name}_prog {{")
     b = src.index("static __device__ __forceinline__ void load_tile", a)
     m = re.search(r"__launch_bounds__\((\d+), \d+\)", src)
-    return src[a:b].replace("sf_pass_spec_prog", "sf_pass_spec_stages") + "};", int(m.group(1)) - 64
+    return src[a:b].replace(f"{name}_prog", "sf_pass_spec_stages") + "};", int(m.group(1)) - 64
 
 
 def _gate_code():
