@@ -326,19 +326,29 @@ def other_configs(sfsim, inputs, peak, stream):
 
 
 # ------------------------------------------------------ runtime model
-def calibrate_runtime_model(sfsim, inputs, stream):
-    """Eq. t_tot's constants fitted on this GPU from measured requests
-    (4 circuits x 3 fidelities x 2 bitstring counts, device timing, best of
-    three each)."""
+def calibrate_runtime_model(sfsim, inputs, stream, extra=()):
+    """Eq. t_tot's constants fitted on this GPU from measured requests, device
+    timing, best of three each: 4 small circuits (halves of 10-18 qubits, in
+    L2) x 3 fidelities x 2 bitstring counts, the 6x7 workload (21-qubit
+    halves) and the 5x10 profiling workload (25-qubit halves) at two
+    fidelities and bitstring counts each, plus `extra` measured points
+    (terms, seconds) - the 7x8 headline steps."""
     import torch
-    T, S = [], []
-    for (R, C, D, cut) in [(5, 6, 24, ("col", 3)), (4, 5, 24, ("col", 2)), (6, 6, 20, ("col", 3)),
-                           (5, 5, 28, ("row", 2))]:
-        mask = (inputs.column_cut_mask if cut[0] == "col" else inputs.row_cut_mask)(R, C, cut[1])
-        plan = sfsim.Plan(inputs.google_circuit(R, C, D, 3).text(), side_b_mask=mask)
-        for f in (1 / 16, 1 / 4, 1.0):
-            for n_a in (10_000, 200_000):
-                bits = inputs.random_bitstrings(R * C, n_a, 11)
+    T, S = [list(t) for t, _ in extra], [s for _, s in extra]
+    cases = [(inputs.google_circuit(R, C, D, 3).text(),
+              (inputs.column_cut_mask if cut[0] == "col" else inputs.row_cut_mask)(R, C, cut[1]), R * C,
+              (1 / 16, 1 / 4, 1.0), (10_000, 200_000))
+             for (R, C, D, cut) in [(5, 6, 24, ("col", 3)), (4, 5, 24, ("col", 2)), (6, 6, 20, ("col", 3)),
+                                    (5, 5, 28, ("row", 2))]]
+    for name, fs, nas in (("6x7_d26", (1 / 1024, 1 / 256), (100_000, 1_000_000)),
+                          ("5x10_d16", (1 / 8, 1 / 2), (100_000, 1_000_000))):
+        wl = inputs.WORKLOADS[name]
+        cases.append((inputs.workload_circuit(name).text(), wl["side_b_mask"], wl["rows"] * wl["cols"], fs, nas))
+    for text, mask, nq, fs, nas in cases:
+        plan = sfsim.Plan(text, side_b_mask=mask)
+        for f in fs:
+            for n_a in nas:
+                bits = inputs.random_bitstrings(nq, n_a, 11)
                 sel = sfsim.selection("fraction", fidelity=f, seed=3)
                 d_bits = torch.from_numpy(bits.view(np.int64)).cuda()
                 d_out = torch.zeros((n_a, 2), dtype=torch.float64, device="cuda")
@@ -355,6 +365,7 @@ def calibrate_runtime_model(sfsim, inputs, stream):
                 S.append(best)
                 T.append(sfsim.sf_plan_cost_terms(plan.handle, sel, n_a))
         plan.close()
+        del ws
     T, S = np.array(T), np.array(S)
     coeffs = sfsim.sf_cost_fit(T, S)
     pred = np.array([sfsim.sf_cost_predict(t, coeffs) for t in T])
@@ -362,6 +373,7 @@ def calibrate_runtime_model(sfsim, inputs, stream):
     return coeffs, {"C0_s": coeffs[0], "C1_s": coeffs[1], "C1C2_s": coeffs[2],
                     "C2": coeffs[2] / coeffs[1] if coeffs[1] > 0 else None, "C3_s": coeffs[3],
                     "requests": len(S), "median_rel_err": float(np.median(rel)), "max_rel_err": float(rel.max()),
+                    "headline_points_rel_err": [float(x) for x in rel[:len(extra)]],
                     "form": "T = C0 + C1 f 2^x_p (q1 2^q1 + q2 2^q2)(d_p + C2 2^x_b d_b) + C3 P n_a (Eq. t_tot, "
                             "plus a fixed cost per request C0)"}
 
@@ -583,6 +595,10 @@ def main():
                     help="1: packed FP32x2 arithmetic in the specialised kernels' Google-gate stages; 0: scalar")
     ap.add_argument("--dense-finals", type=int, default=0, choices=[0, 1],
                     help="1: the final programs write whole final states (no compact blocks)")
+    ap.add_argument("--tile-buffers", type=int, default=0, choices=[0, 2, 3],
+                    help="shared-memory tile buffers per CTA of the specialised kernels (0: per tile size)")
+    ap.add_argument("--proj-side", type=int, default=0, choices=[0, 1],
+                    help="0: Eq. 1's projector on half A of every cut CZ; 1: alternating halves")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1],
                     help="1: per-pass specialised kernels compiled at plan time; 0: the generic pass kernel")
     args = ap.parse_args()
@@ -616,7 +632,8 @@ def main():
     t_plan = time.perf_counter()
     plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode, tile_bits=args.tile_bits,
                       fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit,
-                      split_last=args.split_last, fp32x2=args.fp32x2, dense_finals=args.dense_finals)
+                      split_last=args.split_last, fp32x2=args.fp32x2, dense_finals=args.dense_finals,
+                      projector_side=args.proj_side, tile_buffers=args.tile_buffers)
     t_plan = time.perf_counter() - t_plan
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
@@ -680,6 +697,8 @@ def main():
     e2e_wall = max_over_ranks(time.perf_counter() - t1, f"cuda:{dev}")
     e2e_value = 128 * e2e_steps * world / e2e_wall
 
+    # the headline steps as a point of the runtime model: one 128-path range
+    step_terms = sfsim.sf_plan_cost_terms(plan.handle, sels[args.warmup], len(bits))
     accuracy = None
     if rank == 0 and args.workload == WORKLOAD and len(bits) == w["n_bitstrings"]:
         accuracy = accuracy_7x8(sfsim, plan, bits)
@@ -713,7 +732,7 @@ def main():
     peak, peak_kind = measured_peaks()
     suite = model = serving = None
     if world == 1 and not args.no_suite and args.workload == WORKLOAD:
-        coeffs, model = calibrate_runtime_model(sfsim, inputs, stream)
+        coeffs, model = calibrate_runtime_model(sfsim, inputs, stream, [(step_terms, t_max / args.steps)])
         # the headline request (all f = 0.5% paths, 1M bitstrings) in the model
         mplan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], jit=0, hbm_budget_bytes=1 << 40)
         t7 = sfsim.sf_cost_predict(sfsim.sf_plan_cost_terms(mplan.handle, fsel, len(bits)), coeffs)

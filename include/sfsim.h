@@ -130,8 +130,25 @@ typedef struct {
                                the half and fits the budget; 1 = always write the
                                whole final state */
   int32_t precision;        /* SF_PREC_*: how the cross-path sum accumulates */
-  int32_t reserved;
+  int32_t projector_side;   /* SF_PROJ_*: which half carries Eq. 1's projector */
+  int32_t tile_buffers;     /* specialised kernels: shared-memory tile buffers per
+                               CTA, 3 (load, compute and store each on a buffer of
+                               its own) or 2 (half the memory, so a third CTA of
+                               2^12-amplitude tiles fits on an SM); 0 = 2 for tiles
+                               of up to 2^12 amplitudes, 3 above */
+  int32_t reserved[3];
 } sf_plan_opts;
+
+/* Which half of a cut CZ carries the projector of Eq. 1. CZ is symmetric, so
+ * CZ = P0 (x) I + P1 (x) Z = I (x) P0 + Z (x) P1 (A-side factor first); the
+ * two readings give the same full path sum but different individual paths.
+ *   SF_PROJ_A (default): the projector on the half-A qubit of every cut CZ.
+ *   SF_PROJ_ALTERNATE: on the half-A qubit of the even-numbered cut gates and
+ *     the half-B qubit of the odd-numbered ones (time order (cycle, lower
+ *     qubit, higher qubit), numbered from 0). A projected qubit is a pinned
+ *     index bit, so a branching level's pins are then shared by both halves
+ *     and the passes after it touch fewer amplitudes in total. */
+enum { SF_PROJ_A = 0, SF_PROJ_ALTERNATE = 1 };
 
 /* Precision of the path sum (Section 2 footnote: single-precision states,
  * higher-precision accumulators). The half states are complex64 and each

@@ -4,7 +4,9 @@ A two-qubit gate U acting on (a, b), a in half A and b in half B, is written
 as U = sum_k A_k (x) B_k, with U[(a b), (a' b')] = sum_k A_k[a, a'] B_k[b, b'].
 Each term k is one branch of the path sum.
 
-  projector  - Eq. 1: CZ = P0 (x) I + P1 (x) Z, projector on the A-side qubit.
+  projector  - Eq. 1: CZ = P0 (x) I + P1 (x) Z, projector on the A-side qubit;
+               mirrored (CZ is symmetric): CZ = I (x) P0 + Z (x) P1, projector on
+               the B-side qubit.
   block4     - Eq. 4way: U = P0 (x) U00 + P1 (x) U11 + |0><1| (x) U01 + |1><0| (x) U10,
                U_ij the 2x2 blocks of U indexed by the A-side bits.
   schmidt    - Section 3 / Section 7: the operator-Schmidt decomposition. The
@@ -27,7 +29,9 @@ def oriented(U, a_is_first):
     return U if a_is_first else SWAP @ U @ SWAP
 
 
-def projector_cz():
+def projector_cz(on_b=False):
+    if on_b:
+        return [(gates.I2, gates.P0), (gates.Z, gates.P1)]
     return [(gates.P0, gates.I2), (gates.P1, gates.Z)]
 
 

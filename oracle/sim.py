@@ -75,10 +75,13 @@ class SFSetup:
     """The circuit split by a cut: per-half op lists and the cross-gate terms.
 
     side_b_mask: bit q set <=> qubit q is in half B. decomposition: how non-CZ
-    cross gates are split ('schmidt' or 'block4'); CZ always uses Eq. 1.
+    cross gates are split ('schmidt' or 'block4'); CZ always uses Eq. 1, with
+    the projector on the A-side qubit, or (projector_side='alternate') on the
+    A-side qubit of the even-numbered cross gates (time order, from 0) and the
+    B-side qubit of the odd-numbered ones.
     """
 
-    def __init__(self, circ, side_b_mask, decomposition="schmidt"):
+    def __init__(self, circ, side_b_mask, decomposition="schmidt", projector_side="a"):
         n = circ.n
         self.n = n
         self.posA = np.array([q for q in range(n) if not (side_b_mask >> q) & 1], dtype=np.int32)
@@ -96,11 +99,11 @@ class SFSetup:
         xindex = {gi: k for k, gi in enumerate(cross)}
         self.terms = []
         self.bits = []
-        for gi in cross:
+        for k, gi in enumerate(cross):
             g = circ.gates[gi]
             a_first = not inB(g.qubits[0])
             if g.name == "cz":
-                t = decomp.projector_cz()
+                t = decomp.projector_cz(on_b=projector_side == "alternate" and k % 2 == 1)
             else:
                 U = decomp.oriented(g.mat, a_first)
                 t = decomp.block4(U) if decomposition == "block4" else decomp.schmidt(U)

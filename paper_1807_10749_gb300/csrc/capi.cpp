@@ -191,6 +191,10 @@ int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out)
   if (o.jit != 0 && o.jit != 1) sf::fail(SF_EINVAL, "jit must be 0 or 1");
   if (o.dense_finals != 0 && o.dense_finals != 1) sf::fail(SF_EINVAL, "dense_finals must be 0 or 1");
   if (o.precision != SF_PREC_F64 && o.precision != SF_PREC_COMPENSATED) sf::fail(SF_EINVAL, "unknown precision");
+  if (o.projector_side != SF_PROJ_A && o.projector_side != SF_PROJ_ALTERNATE)
+    sf::fail(SF_EINVAL, "unknown projector side");
+  if (o.tile_buffers != 0 && o.tile_buffers != 2 && o.tile_buffers != 3)
+    sf::fail(SF_EINVAL, "tile_buffers must be 0, 2 or 3");
   sf::Plan* p = sf::plan_create(c->c, o);
   sf_plan* h = new sf_plan();
   h->p = p;

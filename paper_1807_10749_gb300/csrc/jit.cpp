@@ -411,7 +411,7 @@ void gen_stage_cpack(std::ostringstream& o, const PassPlan& pp, const DevStage& 
 
 // One pass as a stage program: struct `name`_prog in namespace sf and an
 // extern "C" kernel `name`.
-std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
+std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack, int nbuf) {
   const DevPass& d = pp.dev;
   const int R = d.R, k = d.k, NR = 1 << R;
   std::ostringstream o;
@@ -641,12 +641,12 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack) {
   gen_copy(o, pp);
   o << "};\n}  // namespace sf\n";
   const int threads = (((1 << (k - R)) + 31) / 32) * 32 + 64;  // stage warps + the two copy warps
-  // tiles of up to 2^12 amplitudes leave shared memory for two CTAs per SM:
-  // ask for the registers to allow it as well
-  const int min_blocks = k <= 12 ? 2 : 1;
+  // tiles of up to 2^12 amplitudes leave shared memory for two CTAs per SM
+  // with three buffers, three CTAs with two: ask for the registers to allow it
+  const int min_blocks = k > 12 ? 1 : (nbuf == 2 ? 3 : 2);
   o << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", " << min_blocks << ") " << name
-    << "(const __grid_constant__ sf::PassLaunch P) {\n  sf::pass_body<" << R << ", sf::" << name
-    << "_prog>(P);\n}\n";
+    << "(const __grid_constant__ sf::PassLaunch P) {\n  sf::pass_body<" << R << ", sf::" << name << "_prog, "
+    << nbuf << ">(P);\n}\n";
   return o.str();
 }
 
@@ -667,6 +667,7 @@ std::string layout_asserts() {
 // -------------------------------------------------------- compiled cache
 struct Entry {
   std::string name;  // the kernel's name
+  int nbuf = 3;      // tile buffers
   std::string src;
   std::string cubin;
   std::string err;
@@ -728,6 +729,14 @@ void compile_entry(Entry* e) {
 
 }  // namespace
 
+// Tile buffers of a pass's kernel: sf_plan_opts.tile_buffers, where 0 = two
+// buffers for tiles of 2^12 amplitudes or fewer (three CTAs per SM) and three
+// above.
+int tile_buffers(const Plan& p, const PassPlan& pp) {
+  if (p.opts.tile_buffers == 2 || p.opts.tile_buffers == 3) return p.opts.tile_buffers;
+  return pp.dev.k <= 12 ? 2 : 3;
+}
+
 // Compile (or find in the cache) a specialised kernel for every pass of the
 // plan; passes get jit_id indexes into p.jit_entries.
 void jit_prepare(Plan& p) {
@@ -757,7 +766,8 @@ void jit_prepare(Plan& p) {
     for (size_t ai = 0; ai < all.size(); ai++) {
       PassPlan* pp = all[ai];
       const char* kname = fin[ai] ? kFinalKernelName : kKernelName;
-      std::string src = gen_pass(*pp, kname, p.opts.fp32x2 != 0);
+      const int nbuf = tile_buffers(p, *pp);
+      std::string src = gen_pass(*pp, kname, p.opts.fp32x2 != 0, nbuf);
       if (dump) {
         const std::string fn = std::string(dump) + "/pass_" + std::to_string(p.jit_entries.size()) + ".cu";
         if (FILE* f = std::fopen(fn.c_str(), "w")) {
@@ -769,6 +779,7 @@ void jit_prepare(Plan& p) {
       if (!slot) {
         slot = std::make_unique<Entry>();
         slot->name = kname;
+        slot->nbuf = nbuf;
         slot->src = src;
         todo.push_back(slot.get());
       }
@@ -801,18 +812,18 @@ void jit_prepare(Plan& p) {
   }
 }
 
-std::string jit_source(const PassPlan& pp) { return gen_pass(pp, kKernelName, true); }
+std::string jit_source(const PassPlan& pp) { return gen_pass(pp, kKernelName, true, 3); }
 
 namespace {
 
 // Threads and dynamic shared memory of a pass launch (the generic kernel's
 // shape): stage warps + the two copy warps; three tile buffers, the run
 // offsets and the nine mbarriers.
-void pass_shape(const DevPass& d, int* threads, size_t* smem) {
+void pass_shape(const DevPass& d, int nbuf, int* threads, size_t* smem) {
   const int nact = 1 << (d.k - d.R);
   *threads = ((nact + 31) / 32) * 32 + 64;
   const int nruns = 1 << (d.k - d.L);
-  *smem = 3 * ((size_t)8 << d.k) + 4 * (size_t)((nruns + 1) & ~1) + 9 * 8;
+  *smem = (size_t)nbuf * ((size_t)8 << d.k) + 4 * (size_t)((nruns + 1) & ~1) + 3 * (size_t)nbuf * 8;
 }
 
 // Load the entry's library and kernel (caller holds g_mu), give it the
@@ -854,8 +865,9 @@ void jit_load(Plan& p) {
       if (pp->jit_id < 0) continue;
       int threads;
       size_t smem;
-      pass_shape(pp->dev, &threads, &smem);
-      ready_entry(static_cast<Entry*>(p.jit_entries[pp->jit_id]), threads, smem);
+      Entry* e = static_cast<Entry*>(p.jit_entries[pp->jit_id]);
+      pass_shape(pp->dev, e->nbuf, &threads, &smem);
+      ready_entry(e, threads, smem);
     }
   }
 }
@@ -866,7 +878,7 @@ void launch_pass_jit(const PassLaunch& L, int tiles, void* entry, void* stream) 
   Entry* e = static_cast<Entry*>(entry);
   int threads;
   size_t smem;
-  pass_shape(L.pass, &threads, &smem);
+  pass_shape(L.pass, e->nbuf, &threads, &smem);
   int nb;
   {
     std::lock_guard<std::mutex> lk(g_mu);

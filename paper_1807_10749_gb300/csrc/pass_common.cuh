@@ -342,9 +342,10 @@ __device__ __forceinline__ void compact_store_tile(const PassLaunch& P, const It
 // same instruction; only active threads (below 2^(k-R)) do stage work.
 // Prog::load_tile / Prog::store_tile move a tile between its node buffer and
 // shared memory (load warp: cp.async into dst; store warp: vector stores).
-template <int R, class Prog>
+// NBUF tile buffers (3: load, compute and store each on their own buffer;
+// 2: half the shared memory, so that more CTAs fit on an SM).
+template <int R, class Prog, int NBUF = 3>
 __device__ __forceinline__ void pass_body(const PassLaunch& P) {
-  constexpr int NBUF = 3;
   extern __shared__ __align__(128) unsigned char smem[];
   const DevPass& d = P.pass;
   const int k = d.k, L = d.L;

@@ -87,7 +87,9 @@ uint64_t auto_cut(const Circuit& c) {
 }
 
 // ---------------------------------------------------------- decompositions
-void decompose(const Gate& g, bool q0_on_a, int decomposition, CrossGate& x) {
+// proj_on_b: for CZ, Eq. 1 with the halves' roles exchanged (CZ is
+// symmetric): CZ = I (x) P0 + Z (x) P1, the projector on the half-B qubit.
+void decompose(const Gate& g, bool q0_on_a, int decomposition, bool proj_on_b, CrossGate& x) {
   const cd I(0, 1);
   cd U[16];
   for (int i = 0; i < 16; i++) U[i] = g.m[i];
@@ -99,10 +101,14 @@ void decompose(const Gate& g, bool q0_on_a, int decomposition, CrossGate& x) {
     for (int i = 0; i < 16; i++) U[i] = V[i];
   }
   std::vector<std::pair<std::array<cd, 4>, std::array<cd, 4>>> terms;
-  if (g.kind == SF_CZ) {
+  if (g.kind == SF_CZ && !proj_on_b) {
     // Eq. 1: CZ = P0 (x) I + P1 (x) Z
     terms.push_back({{1, 0, 0, 0}, {1, 0, 0, 1}});
     terms.push_back({{0, 0, 0, 1}, {1, 0, 0, -1}});
+  } else if (g.kind == SF_CZ) {
+    // Eq. 1 mirrored: CZ = I (x) P0 + Z (x) P1
+    terms.push_back({{1, 0, 0, 1}, {1, 0, 0, 0}});
+    terms.push_back({{1, 0, 0, -1}, {0, 0, 0, 1}});
   } else if (decomposition == SF_DEC_BLOCK4) {
     // Eq. 4way: P0 (x) U00 + P1 (x) U11 + |0><1| (x) U01 + |1><0| (x) U10
     auto blk = [&](int i, int j) {
@@ -825,7 +831,7 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
       bool q0a = !inB(g.q0);
       x.qa = q0a ? g.q0 : g.q1;
       x.qb = q0a ? g.q1 : g.q0;
-      decompose(g, q0a, o.decomposition, x);
+      decompose(g, q0a, o.decomposition, o.projector_side == SF_PROJ_ALTERNATE && (i & 1), x);
       P->cross.push_back(x);
       xindex[xg[i]] = (int)i;
     }

@@ -21,6 +21,7 @@ SF_DEC_SCHMIDT, SF_DEC_BLOCK4 = 0, 1
 SF_EXEC_BATCHED, SF_EXEC_PLAIN = 0, 1
 SF_SEL_RANGE, SF_SEL_FRACTION, SF_SEL_LIST = 0, 1, 2
 SF_PREC_F64, SF_PREC_COMPENSATED = 0, 1
+SF_PROJ_A, SF_PROJ_ALTERNATE = 0, 1
 SF_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 EXPORTED = [
@@ -56,7 +57,9 @@ class sf_plan_opts(ctypes.Structure):
                 ("defer_last_level", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
                 ("batch_paths", ctypes.c_int32), ("run_bits", ctypes.c_int32),
                 ("jit", ctypes.c_int32), ("split_last", ctypes.c_int32), ("fp32x2", ctypes.c_int32),
-                ("dense_finals", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("dense_finals", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("projector_side", ctypes.c_int32), ("tile_buffers", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class sf_path_sel(ctypes.Structure):

@@ -154,6 +154,34 @@ def test_4x4_four_way_branching(kind, dec, jit):
     p.close()
 
 
+def test_alternate_projector_side_each_path(jit):
+    """Eq. 1 mirrored on the odd-numbered cut CZs (projectors, i.e. pinned
+    index bits, on both halves): each of the 16 paths of 4x4 and a 6x7 path
+    list (with a whole folded group) against the oracle under the same
+    reading."""
+    w, text = workload("4x4_d10")
+    c = ocirc.parse(text)
+    setup = sim.SFSetup(c, w["side_b_mask"], projector_side="alternate")
+    bits = inputs.random_bitstrings(16, 1024, w["bitstring_seed"])
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], projector_side=sfsim.SF_PROJ_ALTERNATE)
+    for j in range(16):
+        amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=[j]))
+        check_close(amp, sim.sf_amplitudes(setup, np.array([j], dtype=np.uint64), bits), 16, f"4x4 alt path {j}")
+    p.close()
+    w, text = workload("6x7_d26")
+    c = ocirc.parse(text)
+    setup = sim.SFSetup(c, w["side_b_mask"], projector_side="alternate")
+    bits = inputs.random_bitstrings(42, 4096, w["bitstring_seed"])
+    ids = inputs.random_path_list(setup.x_bits, 16, 12)
+    grp = (int(ids[0]) >> 4) << 4
+    ids = np.unique(np.concatenate([ids, np.arange(grp, grp + 16, dtype=np.uint64)]))
+    per = oracle_per_path(("6x7", "alt"), setup, ids, bits)
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], projector_side=sfsim.SF_PROJ_ALTERNATE)
+    amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
+    check_close(amp, per.sum(axis=0), 42, f"6x7 alt {len(ids)} paths", path_scale=path_scale(per))
+    p.close()
+
+
 def test_tiny_halves_all_paths(jit):
     """Halves of 4 and 6 qubits: tiles smaller than one copy warp's 32 chunks."""
     for (R, C, cut) in [(2, 4, 2), (3, 4, 2)]:

@@ -37,9 +37,30 @@ def test_gate_algebra():
 
 # -------------------------------------------------------------- decompositions
 def test_eq1_projector_decomposition_of_cz():
-    """Eq. 1: CZ = P0 (x) I + P1 (x) Z, exactly."""
+    """Eq. 1: CZ = P0 (x) I + P1 (x) Z, exactly; and mirrored (CZ is
+    symmetric), I (x) P0 + Z (x) P1, with terms that differ from Eq. 1's."""
     rec = decomp.reconstruct(decomp.projector_cz())
     assert np.array_equal(rec, gates.CZ)
+    mir = decomp.projector_cz(on_b=True)
+    assert np.array_equal(decomp.reconstruct(mir), gates.CZ)
+    for (a, b), (c, d) in zip(decomp.projector_cz(), mir):
+        assert not np.array_equal(np.kron(a, b), np.kron(c, d))
+
+
+def test_alternate_projector_side_full_sum_equals_state_vector():
+    """Eq. 2 under the mirrored Eq. 1 on every odd-numbered cut CZ: the sum
+    over all paths is still the exact amplitude, while single paths differ
+    from those of Eq. 1 on the A side (4x4, 1+10+1, all 2^16 bitstrings)."""
+    w = inputs.WORKLOADS["4x4_d10"]
+    c = circ(4, 4, 10)
+    xs = np.arange(1 << 16, dtype=np.uint64)
+    sv = sim.sv_amplitudes(c, xs)
+    alt = sim.SFSetup(c, w["side_b_mask"], projector_side="alternate")
+    std = sim.SFSetup(c, w["side_b_mask"])
+    sf = sim.sf_amplitudes(alt, _all_paths(alt), xs)
+    assert np.abs(sf - sv).max() < 1e-12 * 2 ** -8
+    one = np.array([1], dtype=np.uint64)   # digit 1 on the last (odd-numbered) cut gate
+    assert np.abs(sim.sf_amplitudes(alt, one, xs) - sim.sf_amplitudes(std, one, xs)).max() > 1e-4
 
 
 def test_eq4way_block_decomposition():
