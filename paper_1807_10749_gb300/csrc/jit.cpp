@@ -891,9 +891,20 @@ void launch_pass_jit(const PassLaunch& L, int tiles, void* entry, void* stream) 
   const int64_t items = (int64_t)tiles * L.n_nodes;
   const int64_t grid = std::min<int64_t>(items, (int64_t)sms * nb);
   if (grid < 1) return;
+  // programmatic dependent launch: the kernel waits (griddepcontrol.wait)
+  // for the previous work of the stream before it touches global memory
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   void* args[] = {const_cast<PassLaunch*>(&L)};
-  cudaError_t rc = cudaLaunchKernel((const void*)e->kern, dim3((unsigned)grid), dim3((unsigned)threads), args, smem,
-                                    (cudaStream_t)stream);
+  cudaError_t rc = cudaLaunchKernelExC(&cfg, (const void*)e->kern, args);
   if (rc != cudaSuccess) fail(SF_ECUDA, std::string("specialised pass kernel launch: ") + cudaGetErrorString(rc));
 }
 

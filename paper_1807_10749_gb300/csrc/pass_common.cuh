@@ -391,6 +391,11 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // Launched as a programmatic dependent of the previous pass (the
+  // specialised kernels): the set-up above overlaps that grid's tail; no
+  // thread touches global memory before that grid has completed and its
+  // writes are visible. Without the launch attribute this returns at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == ncw) {
     // --------------------------------------------------------------- loads
@@ -416,6 +421,9 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
       if (lane == 0) mbar_arrive(smem_u32(&full[b]));
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
+    // every tile of this CTA is loaded: the next pass may start its CTAs'
+    // set-up where this grid's CTAs have exited
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     return;
   }
   if (warp == ncw + 1) {
