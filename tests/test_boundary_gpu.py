@@ -214,3 +214,36 @@ def test_compensated_path_sum(c2, jit):
     assert np.abs(_host(out1) - (st[:, 0] + 1j * st[:, 1]) - b).max() <= 1e-12 * scale
     plain.close()
     comp.close()
+
+
+def test_plans_sharing_one_workspace_never_reuse_each_others_nodes(c2):
+    """A plan reuses the path-tree nodes it left in a workspace on its next
+    call; when another plan ran in the same workspace in between, nothing is
+    reused. Two plans (5x6 and 4x5) alternate on one workspace; each call
+    equals the same call on a fresh workspace, bit for bit."""
+    import torch
+    plan_a, _, _ = c2
+    mask_b = inputs.column_cut_mask(4, 5, 2)
+    plan_b = sfsim.Plan(inputs.google_circuit(4, 5, 20, 2).text(), side_b_mask=mask_b)
+    bits_a = inputs.random_bitstrings(30, 2000, 61)
+    bits_b = inputs.random_bitstrings(20, 2000, 62)
+    sel = [sfsim.selection("range", first=1024 * i, count=512) for i in range(3)]
+    want_a = [_device_call(plan_a, bits_a, s) for s in sel]
+    want_b = [_device_call(plan_b, bits_b, s) for s in sel]
+    need = max(sfsim.sf_workspace_size(p.handle, 2000, s) for p in (plan_a, plan_b) for s in sel)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    da, db = _dev(bits_a), _dev(bits_b)
+    for i, s in enumerate(sel):
+        for plan, d_bits, want in ((plan_a, da, want_a), (plan_b, db, want_b)):
+            d_out = torch.zeros((2000, 2), dtype=torch.float64, device="cuda")
+            sfsim.sf_amplitudes_device(plan.handle, d_bits, s, d_out, ws)
+            assert np.array_equal(_host(d_out), want[i])
+    # the caller overwrites the workspace: after sf_plan_drop_resident the
+    # plan recomputes everything
+    sfsim.sf_amplitudes_device(plan_a.handle, da, sel[0], torch.zeros((2000, 2), dtype=torch.float64, device="cuda"), ws)
+    ws.fill_(0x7f)
+    sfsim.sf_plan_drop_resident(plan_a.handle)
+    d_out = torch.zeros((2000, 2), dtype=torch.float64, device="cuda")
+    sfsim.sf_amplitudes_device(plan_a.handle, da, sel[0], d_out, ws)
+    assert np.array_equal(_host(d_out), want_a[0])
+    plan_b.close()
