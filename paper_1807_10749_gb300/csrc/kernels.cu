@@ -266,17 +266,36 @@ __device__ __forceinline__ uint32_t compact_index(const CompactMap& c, uint32_t 
   return h | (j & ((1u << c.ctl) - 1u));
 }
 
-template <int G>
-__global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherLaunch P) {
+// ALL: every final of the launch sums all leaves of its folded group (the
+// closed-form contraction only; fewer registers).
+template <int G, bool ALL>
+__global__ void __launch_bounds__(256, 2) gather_kernel(const __grid_constant__ GatherLaunch P) {
   __shared__ uint32_t tA[8 * 256], tB[8 * 256];
+  // the folded level's 2x2 contraction matrices K_t[y, z] = sum_d MA_{t,d}[xa, y]
+  // MB_{t,d}[xb, z] for every deferred gate t and bit pair (xa, xb): formed once
+  // per CTA, not per bitstring
+  __shared__ float2 Ks[G > 0 ? G : 1][4][2][2];
   for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) {
     tA[i] = P.tabA[i];
     tB[i] = P.tabB[i];
   }
-  __syncthreads();
   const int NY = 1 << G;
   const int tb = P.nterm_bits;
   const int nt = 1 << tb;
+  if (G > 0 && threadIdx.x < G * 16) {
+    const int t = threadIdx.x >> 4, ab = (threadIdx.x >> 2) & 3, y = (threadIdx.x >> 1) & 1, z = threadIdx.x & 1;
+    const int xa_ = ab >> 1, xb_ = ab & 1;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int dd = 0; dd < nt; dd++) {
+      const float* ma = P.ma[t][dd];
+      const float* mb = P.mb[t][dd];
+      float2 a = make_float2(ma[2 * (2 * xa_ + y)], ma[2 * (2 * xa_ + y) + 1]);
+      float2 b = make_float2(mb[2 * (2 * xb_ + z)], mb[2 * (2 * xb_ + z) + 1]);
+      acc = cadd(acc, cmul(a, b));
+    }
+    Ks[t][ab][y][z] = acc;
+  }
+  __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t x = P.bits[i];
@@ -324,54 +343,61 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       }
       const float2* WA = reinterpret_cast<const float2*>(F.wa);
       const float2* WB = reinterpret_cast<const float2*>(F.wb);
-      float2 wa[1 << G], wb[1 << G];
+      auto load_a = [&](int y) {
+        uint32_t ja = ia;
+#pragma unroll
+        for (int t = 0; t < G; t++) ja |= (uint32_t)((y >> t) & 1) << P.A.dpos[t];
+        return ((ja & pam) == pav) ? WA[compact_index(P.A.c, ha0, ha1, ja)] : make_float2(0.f, 0.f);
+      };
+      float2 wb[1 << G];
 #pragma unroll
       for (int y = 0; y < NY; y++) {
-        uint32_t ja = ia, jb = ib;
+        uint32_t jb = ib;
 #pragma unroll
-        for (int t = 0; t < G; t++) {
-          ja |= (uint32_t)((y >> t) & 1) << P.A.dpos[t];
-          jb |= (uint32_t)((y >> t) & 1) << P.B.dpos[t];
-        }
-        wa[y] = ((ja & pam) == pav) ? WA[compact_index(P.A.c, ha0, ha1, ja)] : make_float2(0.f, 0.f);
+        for (int t = 0; t < G; t++) jb |= (uint32_t)((y >> t) & 1) << P.B.dpos[t];
         wb[y] = ((jb & pbm) == pbv) ? WB[compact_index(P.B.c, hb0, hb1, jb)] : make_float2(0.f, 0.f);
       }
       float2 c = make_float2(0.f, 0.f);
-      if (G == 0) {
-        c = cmul(wa[0], wb[0]);
-      } else if (F.all_leaves) {
-        // sum over every leaf: contract wb with K_t[y, z] = sum_d MA_{t,d}[xa_t, y] MB_{t,d}[xb_t, z]
-        float2 tv[1 << G];
-#pragma unroll
-        for (int z = 0; z < NY; z++) tv[z] = wb[z];
+      if constexpr (ALL && G > 0) {
+        // every leaf of the group: contract wb (in place) with K_t[y, z] =
+        // sum_d MA_{t,d}[xa_t, y] MB_{t,d}[xb_t, z], then dot with wa read
+        // one amplitude at a time
 #pragma unroll
         for (int t = 0; t < G; t++) {
-          float2 K[2][2];
-#pragma unroll
-          for (int y = 0; y < 2; y++)
-#pragma unroll
-            for (int z = 0; z < 2; z++) {
-              float2 acc = make_float2(0.f, 0.f);
-              for (int dd = 0; dd < nt; dd++) {
-                const float* ma = P.ma[t][dd];
-                const float* mb = P.mb[t][dd];
-                float2 a = make_float2(ma[2 * (2 * xa[t] + y)], ma[2 * (2 * xa[t] + y) + 1]);
-                float2 b = make_float2(mb[2 * (2 * xb[t] + z)], mb[2 * (2 * xb[t] + z) + 1]);
-                acc = cadd(acc, cmul(a, b));
-              }
-              K[y][z] = acc;
-            }
+          const float2(&K)[2][2] = Ks[t][2 * xa[t] + xb[t]];
 #pragma unroll
           for (int y = 0; y < NY; y++) {
             if (y & (1 << t)) continue;
-            const float2 t0 = tv[y], t1 = tv[y | (1 << t)];
-            tv[y] = cadd(cmul(K[0][0], t0), cmul(K[0][1], t1));
-            tv[y | (1 << t)] = cadd(cmul(K[1][0], t0), cmul(K[1][1], t1));
+            const float2 t0 = wb[y], t1 = wb[y | (1 << t)];
+            wb[y] = cadd(cmul(K[0][0], t0), cmul(K[0][1], t1));
+            wb[y | (1 << t)] = cadd(cmul(K[1][0], t0), cmul(K[1][1], t1));
           }
         }
 #pragma unroll
-        for (int y = 0; y < NY; y++) c = cadd(c, cmul(wa[y], tv[y]));
+        for (int y = 0; y < NY; y++) c = cadd(c, cmul(load_a(y), wb[y]));
       } else {
+      float2 wa[1 << G];
+#pragma unroll
+      for (int y = 0; y < NY; y++) wa[y] = load_a(y);
+      if (G == 0) {
+        c = cmul(wa[0], wb[0]);
+      } else if (ALL || F.all_leaves) {
+        // sum over every leaf: contract wb (in place) with K_t[y, z] = sum_d
+        // MA_{t,d}[xa_t, y] MB_{t,d}[xb_t, z]
+#pragma unroll
+        for (int t = 0; t < G; t++) {
+          const float2(&K)[2][2] = Ks[t][2 * xa[t] + xb[t]];
+#pragma unroll
+          for (int y = 0; y < NY; y++) {
+            if (y & (1 << t)) continue;
+            const float2 t0 = wb[y], t1 = wb[y | (1 << t)];
+            wb[y] = cadd(cmul(K[0][0], t0), cmul(K[0][1], t1));
+            wb[y | (1 << t)] = cadd(cmul(K[1][0], t0), cmul(K[1][1], t1));
+          }
+        }
+#pragma unroll
+        for (int y = 0; y < NY; y++) c = cadd(c, cmul(wa[y], wb[y]));
+      } else if constexpr (!ALL) {
         const int nleaf = 1 << (G * tb);
         for (int b = 0; b < nleaf; b++) {
           if (!((F.leafmask[b >> 6] >> (b & 63)) & 1ull)) continue;
@@ -393,6 +419,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
           }
           c = cadd(c, cmul(av, bv));
         }
+      }
       }
       const double tr = (double)c.x * F.sre - (double)c.y * F.sim;
       const double ti = (double)c.x * F.sim + (double)c.y * F.sre;
@@ -629,14 +656,18 @@ void launch_gather(const GatherLaunch& L, void* stream) {
   int64_t blocks = (L.n + threads - 1) / threads;
   int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
+  bool all = true;
+  for (int f = 0; f < L.n_finals; f++) all = all && L.finals[f].all_leaves;
+#define SF_G(GG)                                                                   \
+  case GG:                                                                         \
+    if (all) gather_kernel<GG, true><<<(int)blocks, threads, 0, s>>>(L);           \
+    else gather_kernel<GG, false><<<(int)blocks, threads, 0, s>>>(L);              \
+    break;
   switch (L.g) {
-    case 0: gather_kernel<0><<<(int)blocks, threads, 0, s>>>(L); break;
-    case 1: gather_kernel<1><<<(int)blocks, threads, 0, s>>>(L); break;
-    case 2: gather_kernel<2><<<(int)blocks, threads, 0, s>>>(L); break;
-    case 3: gather_kernel<3><<<(int)blocks, threads, 0, s>>>(L); break;
-    case 4: gather_kernel<4><<<(int)blocks, threads, 0, s>>>(L); break;
+    SF_G(0) SF_G(1) SF_G(2) SF_G(3) SF_G(4)
     default: fail(SF_EINVAL, "internal: too many deferred gates");
   }
+#undef SF_G
   check(cudaGetLastError(), "gather_kernel launch");
 }
 
@@ -766,8 +797,10 @@ void preload_kernels() {
       (const void*)pass_kernel<1, false>, (const void*)pass_kernel<2, false>, (const void*)pass_kernel<3, false>,
       (const void*)pass_kernel<4, false>, (const void*)pass_kernel<5, false>, (const void*)pass_kernel<1, true>,
       (const void*)pass_kernel<2, true>,  (const void*)pass_kernel<3, true>,  (const void*)pass_kernel<4, true>,
-      (const void*)pass_kernel<5, true>,  (const void*)gather_kernel<0>,      (const void*)gather_kernel<1>,
-      (const void*)gather_kernel<2>,      (const void*)gather_kernel<3>,      (const void*)gather_kernel<4>,
+      (const void*)pass_kernel<5, true>,  (const void*)gather_kernel<0, false>, (const void*)gather_kernel<1, false>,
+      (const void*)gather_kernel<2, false>, (const void*)gather_kernel<3, false>, (const void*)gather_kernel<4, false>,
+      (const void*)gather_kernel<0, true>, (const void*)gather_kernel<1, true>,  (const void*)gather_kernel<2, true>,
+      (const void*)gather_kernel<3, true>, (const void*)gather_kernel<4, true>,
       (const void*)frugal_accept_kernel,  (const void*)block_mark_kernel,     (const void*)block_count_kernel,
       (const void*)block_rank_kernel,     (const void*)zero_kernel,           (const void*)fold_kernel,
       (const void*)prob_kernel,           (const void*)overlap_kernel,        (const void*)overlap_finish_kernel};

@@ -44,7 +44,7 @@ def _gather_index_code():
     a = h.index("struct CompactMap {")
     b = h.index("struct GatherSide {")
     c = k.index("__device__ __forceinline__ uint32_t compact_part(")
-    d = k.index("template <int G>", c)
+    d = k.index("template <int G, bool ALL>", c)
     return h[a:b] + k[c:d]
 
 
