@@ -595,6 +595,8 @@ def main():
                     help="1: packed FP32x2 arithmetic in the specialised kernels' Google-gate stages; 0: scalar")
     ap.add_argument("--dense-finals", type=int, default=0, choices=[0, 1],
                     help="1: the final programs write whole final states (no compact blocks)")
+    ap.add_argument("--batch-paths", type=int, default=0,
+                    help="finals (leaf groups) per block of the executor, 0: from the memory budget")
     ap.add_argument("--tile-buffers", type=int, default=0, choices=[0, 2, 3],
                     help="shared-memory tile buffers per CTA of the specialised kernels (0: per tile size)")
     ap.add_argument("--proj-side", type=int, default=0, choices=[0, 1],
@@ -633,7 +635,8 @@ def main():
     plan = sfsim.Plan(text, side_b_mask=w["side_b_mask"], exec_mode=mode, tile_bits=args.tile_bits,
                       fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit,
                       split_last=args.split_last, fp32x2=args.fp32x2, dense_finals=args.dense_finals,
-                      projector_side=args.proj_side, tile_buffers=args.tile_buffers)
+                      projector_side=args.proj_side, tile_buffers=args.tile_buffers,
+                      batch_paths=args.batch_paths)
     t_plan = time.perf_counter() - t_plan
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)
