@@ -128,6 +128,11 @@ struct PassLaunch {
   uint8_t xshift[MAX_CROSS];
   uint8_t xbits[MAX_CROSS];
   int* err;        // set to 1 if a bounded wait gave up
+  // Work distribution: work[0] hands out the items after each CTA's first
+  // (item = gridDim.x + atomicAdd(work, 1)), work[1] counts the CTAs that
+  // have taken their last; the last of them sets both back to zero, so they
+  // are zero at the start of every launch (the caller zeroes them once).
+  uint32_t* work;
   // Compact output (final passes whose result only the gather reads): null =
   // every live amplitude is written at its index. Otherwise only requested
   // parts are written. A part is a tile's share of one block of the gather

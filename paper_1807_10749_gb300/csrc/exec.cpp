@@ -147,10 +147,15 @@ int cached_depths(const Plan& p) {
   return p.merged_last ? nL - 1 : nL;
 }
 
+// Bytes at the end of the workspace for the pass kernels' work counters.
+constexpr size_t kWorkBytes = 256;
+
 // extra: fixed bytes after the rest (the compensation terms of
-// SF_PREC_COMPENSATED), counted against the budget.
+// SF_PREC_COMPENSATED), counted against the budget; the work counters
+// follow them.
 Layout make_layout(const Plan& p, uint64_t n_finals, const Compact& cp, int64_t budget_override = 0,
                    size_t extra = 0) {
+  extra += kWorkBytes;
   const int nL = cached_depths(p);
   const size_t nb = node_bytes(p);
   int64_t budget = budget_override > 0 ? budget_override : p.opts.hbm_budget_bytes;
@@ -198,13 +203,14 @@ uint64_t count_finals(const Plan& p, const std::vector<Range>& rs) {
   return n;
 }
 
-void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan, int* err) {
+void fill_launch(PassLaunch& L, const PassPlan& pp, const Plan& plan, int* err, uint32_t* work) {
   static_assert(sizeof(PassLaunch) <= 32764, "kernel parameter block too large");
   if (pp.stages.size() > (size_t)MAX_STAGES || pp.ops.size() > (size_t)MAX_OPS ||
       pp.phases.size() > (size_t)MAX_PHASE_GROUPS || pp.mats.size() > (size_t)2 * MAX_MATS)
     fail(SF_EUNSUPPORTED, "internal: pass program too large");
   L.pass = pp.dev;
   L.err = err;
+  L.work = work;
   L.cmap = nullptr;
   L.ctl = L.cpad = 0;
   std::copy(pp.stages.begin(), pp.stages.end(), L.stages);
@@ -279,7 +285,7 @@ struct CompactOut {
 
 // Run a segment program for a batch of nodes of one half.
 void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<Job>& jobs,
-                 cudaStream_t st, bool prof, int* err, const CompactOut* co = nullptr) {
+                 cudaStream_t st, bool prof, int* err, uint32_t* work, const CompactOut* co = nullptr) {
   if (jobs.empty()) return;
   if (co && co->out.size() != jobs.size()) fail(SF_EINVAL, "internal: compact outputs");
   for (size_t p = 0; p < seg.passes.size(); p++) {
@@ -291,7 +297,7 @@ void run_segment(Cache&, Plan& plan, const SegmentPlan& seg, const std::vector<J
       std::memset(scratch.get(), 0, sizeof(PassLaunch));
     }
     PassLaunch* L = scratch.get();
-    fill_launch(*L, pp, plan, err);
+    fill_launch(*L, pp, plan, err, work);
     if (compact) {
       L->cmap = co->cmap;
       L->ctl = co->ctl;
@@ -587,8 +593,11 @@ void exec_run(Plan& plan, std::vector<ExecReq>& reqs, void* ws, size_t ws_bytes,
   const SegmentPlan& finB =
       plan.merged_last ? plan.B.last_merged : (plan.deferred ? plan.B.last_deferred : plan.B.seg[nL]);
 
+  // the pass kernels' work counters (the last bytes), zeroed once per call
+  uint32_t* work = reinterpret_cast<uint32_t*>(base + (lay.bytes - kWorkBytes));
+  launch_zero(reinterpret_cast<double*>(work), 1, st);
   // compensation terms of each request (after everything else), zeroed
-  char* comp_at = base + (lay.bytes - cb);
+  char* comp_at = base + (lay.bytes - kWorkBytes - cb);
   std::vector<double*> comp(reqs.size(), nullptr);
   if (compensated)
     for (size_t q = 0; q < reqs.size(); q++) {
@@ -794,8 +803,8 @@ void exec_run(Plan& plan, std::vector<ExecReq>& reqs, void* ws, size_t ws_bytes,
           }
           computed.push_back(freep);
         }
-        run_segment(*C, plan, plan.A.seg[s], jobsA, st, prof, err);
-        run_segment(*C, plan, plan.B.seg[s], jobsB, st, prof, err);
+        run_segment(*C, plan, plan.A.seg[s], jobsA, st, prof, err, work);
+        run_segment(*C, plan, plan.B.seg[s], jobsB, st, prof, err, work);
         for (size_t q : computed) slots[q].valid = true;
         prev_ids = ids;
         prev_slot = where;
@@ -857,8 +866,8 @@ void exec_run(Plan& plan, std::vector<ExecReq>& reqs, void* ws, size_t ws_bytes,
           gf[w.first].push_back(g);
         }
       }
-      run_segment(*C, plan, finA, jobsA, st, prof, err, cmap[0] ? &coA : nullptr);
-      run_segment(*C, plan, finB, jobsB, st, prof, err, cmap[1] ? &coB : nullptr);
+      run_segment(*C, plan, finA, jobsA, st, prof, err, work, cmap[0] ? &coA : nullptr);
+      run_segment(*C, plan, finB, jobsB, st, prof, err, work, cmap[1] ? &coB : nullptr);
       if (plan.opts.exec_mode == SF_EXEC_PLAIN) {
         // the plain form shares nothing below the selection prefix: every
         // path re-evolves its levels under the prefix checkpoint

@@ -97,6 +97,98 @@ std::string f2lit(const std::vector<float>& m, int i) {  // float2 at float inde
   return "make_float2(" + flit(m[2 * i]) + ", " + flit(m[2 * i + 1]) + ")";
 }
 
+// ---- per-pass tile swizzle -------------------------------------------------
+// A tile element e lives in shared memory at e ^ (f(e) << 1), where f is a
+// linear map from index bits 4 and up into three bits: bit q of f(e) is the
+// parity of e & m[q]. Such a swizzle is a bijection of the tile that keeps
+// 16-byte chunks (element pairs) whole, so the copy warps are unaffected;
+// the default (m = bits 4,7,10 / 5,8,11 / 6,9,12) is dev_types.h's swz().
+// A stage thread's accesses are one base address plus a constant per
+// register slot, the lanes varying in the stage's five lowest thread bits.
+// An 8-byte access of a warp is served per half warp (lanes 0-15: the
+// lowest four thread bits) and is conflict-free when those lanes fall into
+// 16 distinct bank pairs: the four bits' images in address bits 0..3 are
+// independent. A 16-byte access (tile bit 0 in registers) is served per
+// quarter warp: three bits' images in address bits 1..3. Each pass takes
+// the swizzle that makes every one of its stages conflict-free, searched
+// from the default in a fixed pseudo-random order (the default is kept when
+// it already is).
+struct TileSwz {
+  uint32_t m[3];
+  uint32_t operator()(uint32_t e) const {
+    uint32_t r = e;
+    for (int q = 0; q < 3; q++) r ^= (uint32_t)(__builtin_popcount(e & m[q]) & 1) << (1 + q);
+    return r;
+  }
+  bool is_default() const {
+    return m[0] == 0x490u && m[1] == 0x920u && m[2] == 0x1240u;
+  }
+};
+
+TileSwz default_swz() { return TileSwz{{0x490u, 0x920u, 0x1240u}}; }
+
+int gf2_rank(uint32_t* v, int n) {
+  int r = 0;
+  for (int bit = 31; bit >= 0 && r < n; bit--) {
+    int piv = -1;
+    for (int i = r; i < n; i++)
+      if ((v[i] >> bit) & 1) piv = i;
+    if (piv < 0) continue;
+    std::swap(v[r], v[piv]);
+    for (int i = 0; i < n; i++)
+      if (i != r && ((v[i] >> bit) & 1)) v[i] ^= v[r];
+    r++;
+  }
+  return r;
+}
+
+// Excess shared-memory wavefronts of the pass's stage accesses (0: none).
+int swz_excess(const PassPlan& pp, const TileSwz& S) {
+  const DevPass& d = pp.dev;
+  const int k = d.k, R = d.R;
+  int excess = 0;
+  for (int s = 0; s < d.n_stages; s++) {
+    const DevStage& st = pp.stages[s];
+    bool wide = false;  // tile bit 0 in registers: 16-byte accesses
+    for (int j = 0; j < R; j++)
+      if (st.rbit[j] == 0) wide = true;
+    const int nb = wide ? 3 : 4;
+    if (k - R < nb) continue;
+    uint32_t v[4];
+    for (int t = 0; t < nb; t++) {
+      const uint32_t a = S(1u << st.tpos[t]);
+      v[t] = wide ? (a >> 1) & 7u : a & 15u;
+    }
+    excess += (1 << (nb - gf2_rank(v, nb))) - 1;
+  }
+  return excess;
+}
+
+TileSwz choose_swz(const PassPlan& pp) {
+  TileSwz best = default_swz();
+  const int k = pp.dev.k;
+  if (k < 8) return best;  // tiles of the generic copy loops keep the default
+  int be = swz_excess(pp, best);
+  uint64_t x = 0x9e3779b97f4a7c15ull;
+  for (int it = 0; it < 4096 && be > 0; it++) {
+    TileSwz c{{0u, 0u, 0u}};
+    for (int b = 4; b < k; b++) {
+      x ^= x << 13;
+      x ^= x >> 7;
+      x ^= x << 17;
+      const uint32_t f = (uint32_t)(x >> 61);  // three bits
+      for (int q = 0; q < 3; q++)
+        if ((f >> q) & 1) c.m[q] |= 1u << b;
+    }
+    const int e = swz_excess(pp, c);
+    if (e < be) {
+      be = e;
+      best = c;
+    }
+  }
+  return best;
+}
+
 // thread-index bits t -> bit positions pos[t], grouped into shifted fields
 std::string deposit(const int8_t* pos, int nbits) {
   std::string e;
@@ -120,7 +212,7 @@ std::string deposit(const int8_t* pos, int nbits) {
 // (swz(2l) ^ lo_j) | 64 j, with lo_j the swizzle's bits 1..3 for the j part:
 // one base per distinct lo_j plus a constant. Runs with a pinned bit other
 // than the tile's value are skipped (structural zeros).
-void gen_copy(std::ostringstream& o, const PassPlan& pp) {
+void gen_copy(std::ostringstream& o, const PassPlan& pp, const TileSwz& S) {
   const DevPass& d = pp.dev;
   if (d.k < 6) {  // fewer chunks than lanes: the generic loops
     o << "static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, "
@@ -149,7 +241,7 @@ void gen_copy(std::ostringstream& o, const PassPlan& pp) {
     for (int b = 6; b < k; b++)
       if ((e >> b) & 1) g |= 1u << d.gpos[b];
     G[j] = g;
-    lo[j] = swz(e) & 0xFu;
+    lo[j] = S(e) & 0xFu;
     rj[j] = e >> L;
     int q = 0;
     while (q < nlow && lows[q] != lo[j]) q++;
@@ -414,8 +506,17 @@ void gen_stage_cpack(std::ostringstream& o, const PassPlan& pp, const DevStage& 
 std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack, int nbuf) {
   const DevPass& d = pp.dev;
   const int R = d.R, k = d.k, NR = 1 << R;
+  const TileSwz S = choose_swz(pp);
   std::ostringstream o;
-  o << "namespace sf {\nstruct " << name << "_prog {\n"
+  o << "namespace sf {\nstruct " << name << "_prog {\n";
+  if (S.is_default()) {
+    o << "static __device__ __forceinline__ uint32_t swz(uint32_t e) { return sf::swz(e); }\n";
+  } else {
+    o << "static __device__ __forceinline__ uint32_t swz(uint32_t e) {\n  return e";
+    for (int q = 0; q < 3; q++) o << " ^ ((uint32_t)(__popc(e & " << S.m[q] << "u) & 1) << " << 1 + q << ")";
+    o << ";\n}\n";
+  }
+  o
     << "static __device__ __forceinline__ void run(const PassLaunch& P, float2* sm, const ItemGeo& g, "
        "const float2* w8, int ncomp, bool active) {\n"
     << "const uint32_t tid = threadIdx.x;\n(void)P; (void)g; (void)w8;\n";
@@ -427,7 +528,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack, int
     for (int i = 0; i < NR; i++) {
       uint32_t c = 0;
       for (int j = 0; j < R; j++)
-        if ((i >> j) & 1) c ^= swz(1u << st.rbit[j]);
+        if ((i >> j) & 1) c ^= S(1u << st.rbit[j]);
       C[i] = c;
     }
     for (int j = 0; j < R; j++) gr[j] = d.gpos[st.rbit[j]];
@@ -638,7 +739,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack, int
     o << "}\ncompute_bar(ncomp);\n";
   }
   o << "}\n";
-  gen_copy(o, pp);
+  gen_copy(o, pp, S);
   o << "};\n}  // namespace sf\n";
   const int threads = (((1 << (k - R)) + 31) / 32) * 32 + 64;  // stage warps + the two copy warps
   // tiles of up to 2^12 amplitudes leave shared memory for two CTAs per SM

@@ -236,8 +236,11 @@ struct CopyCtx {
   uint32_t lmask;
 };
 
-// The generic copy loops: four 16-byte chunks in flight per lane.
+// The generic copy loops: four 16-byte chunks in flight per lane. They use
+// the default tile swizzle; a stage program with its own swizzle defines
+// swz() and its own copies.
 struct GenericCopy {
+  static __device__ __forceinline__ uint32_t swz(uint32_t e) { return sf::swz(e); }
   static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, int lane,
                                                    const CopyCtx& cc) {
     const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
@@ -310,6 +313,8 @@ __device__ __forceinline__ CompactWord compact_word(const PassLaunch& P, const I
   return cw;
 }
 
+// SW::swz is the tile's shared-memory swizzle.
+template <class SW>
 __device__ __forceinline__ void compact_write(const PassLaunch& P, const ItemGeo& g, const float2* buf, int lane,
                                               int r, const CompactWord& cw) {
   float2* out = reinterpret_cast<float2*>(P.nodes[g.node].out);
@@ -324,17 +329,18 @@ __device__ __forceinline__ void compact_write(const PassLaunch& P, const ItemGeo
     const uint32_t slot = cw.rank + (uint32_t)__popc(cw.bits & ((1u << j) - 1u));
     float4* dst = reinterpret_cast<float4*>(out + ((uint64_t)slot << tl));
     const uint32_t c0 = (ub + j) << (tl - 1);
-    for (int q = 0; q < nq; q++) dst[q] = srcb[swz(2u * (c0 + (uint32_t)q)) >> 1];
+    for (int q = 0; q < nq; q++) dst[q] = srcb[SW::swz(2u * (c0 + (uint32_t)q)) >> 1];
   }
 }
 
 // cw: the lane's words of round 0 (compact_word(P, g, lane, 0)).
+template <class SW>
 __device__ __forceinline__ void compact_store_tile(const PassLaunch& P, const ItemGeo& g, const float2* buf,
                                                    int lane, const CompactWord& cw) {
   const int kt = P.pass.k - P.ctl;
   const int rounds = kt > 10 ? 1 << (kt - 10) : 1;
-  compact_write(P, g, buf, lane, 0, cw);
-  for (int r = 1; r < rounds; r++) compact_write(P, g, buf, lane, r, compact_word(P, g, lane, r));
+  compact_write<SW>(P, g, buf, lane, 0, cw);
+  for (int r = 1; r < rounds; r++) compact_write<SW>(P, g, buf, lane, r, compact_word(P, g, lane, r));
 }
 
 // Prog::run(P, sm, g, w8, ncomp, active) runs the register stages of one
@@ -399,11 +405,18 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
 
   if (warp == ncw) {
     // --------------------------------------------------------------- loads
-    // The load warp also computes each item's geometry once and publishes it
-    // in geo[b]; lane 0's arrive (release) on full[b] orders it before the
-    // compute and store warps' waits (acquire) on that barrier.
-    int i = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
+    // The load warp takes the CTA's items: its first is blockIdx.x, every
+    // later one comes from the launch's counter (taken one item ahead, so
+    // the atomic's latency hides behind the wait for a free buffer). CTAs
+    // that get through their items faster take more of them, so the CTAs
+    // sharing an SM finish together. The warp computes each item's geometry
+    // once and publishes it in geo[b]; after the last item it publishes an
+    // end marker (node -1) the same way. Lane 0's arrive (release) on
+    // full[b] orders geo[b] before the compute and store warps' waits
+    // (acquire) on that barrier.
+    int64_t it = blockIdx.x;
+    uint32_t ahead = 0;  // lane 0: the counter's value for the next item
+    for (int i = 0;; i++) {
       const int b = i % NBUF;
       if (i >= NBUF && !mbar_wait(smem_u32(&freeb[b]), (uint32_t)((i / NBUF - 1) & 1))) {
         if (lane == 0) {
@@ -413,12 +426,29 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         break;
       }
       if (*(volatile int*)&abort_flag) break;
-      const ItemGeo g = item_geo(P, it, tiles_log2);
+      if (i > 0) it = (int64_t)gridDim.x + (int64_t)__shfl_sync(0xffffffffu, ahead, 0);
+      const bool last = it >= items;
+      if (lane == 0 && !last) ahead = atomicAdd(P.work, 1u);
+      ItemGeo g{};
+      if (!last) g = item_geo(P, it, tiles_log2);
+      else g.node = -1;
       if (lane == 0) geo[b] = g;
-      if (!d.gen_input) Prog::load_tile(P, g, smem_u32(bufs + b * ntile), lane, cc);
+      if (!last && !d.gen_input) Prog::load_tile(P, g, smem_u32(bufs + b * ntile), lane, cc);
       cp_async_arrive(smem_u32(&full[b]));
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&full[b]));
+      if (last) {
+        // this CTA takes no more items; the last CTA to get here resets the
+        // counters for the next launch (every other CTA has taken its last)
+        if (lane == 0) {
+          __threadfence();
+          if (atomicAdd(P.work + 1, 1u) == gridDim.x - 1u) {
+            atomicExch(P.work, 0u);
+            atomicExch(P.work + 1, 0u);
+          }
+        }
+        break;
+      }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     // every tile of this CTA is loaded: the next pass may start its CTAs'
@@ -428,19 +458,17 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
   }
   if (warp == ncw + 1) {
     // -------------------------------------------------------------- stores
-    int i = 0;
-    for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
+    for (int i = 0;; i++) {
       const int b = i % NBUF;
       const uint32_t par = (uint32_t)((i / NBUF) & 1);
-      // compact output: the geometry is readable once full[b] completes
-      // (buffer b cannot be refilled before this warp frees it), so load
-      // the tile's part-map words while the tile is being computed
+      // the geometry is readable once full[b] completes (buffer b cannot be
+      // refilled before this warp frees it); for a compact output, load the
+      // tile's part-map words while the tile is being computed
+      bool ok = mbar_wait(smem_u32(&full[b]), par);
+      const ItemGeo g = geo[b];
+      if (ok && g.node < 0) break;  // end marker
       CompactWord cw{0u, 0u};
-      bool ok = true;
-      if (P.cmap) {
-        ok = mbar_wait(smem_u32(&full[b]), par);
-        if (ok) cw = compact_word(P, geo[b], lane, 0);
-      }
+      if (ok && P.cmap) cw = compact_word(P, g, lane, 0);
       if (!ok || !mbar_wait(smem_u32(&empty[b]), par) || *(volatile int*)&abort_flag) {
         if (lane == 0) {
           abort_flag = 1;
@@ -448,8 +476,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         }
         break;
       }
-      const ItemGeo g = geo[b];
-      if (P.cmap) compact_store_tile(P, g, bufs + b * ntile, lane, cw);
+      if (P.cmap) compact_store_tile<Prog>(P, g, bufs + b * ntile, lane, cw);
       else Prog::store_tile(P, g, bufs + b * ntile, lane, cc);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&freeb[b]));
@@ -458,8 +485,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
   }
 
   // -------------------------------------------------------------- compute
-  int i = 0;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x, i++) {
+  for (int i = 0;; i++) {
     const int b = i % NBUF;
     float2* sm = bufs + b * ntile;
     const bool timed_out = !mbar_wait(smem_u32(&full[b]), (uint32_t)((i / NBUF) & 1));
@@ -471,13 +497,14 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
       break;
     }
     const ItemGeo g = geo[b];
+    if (g.node < 0) break;  // end marker (the same for every compute warp)
     if (d.gen_input) {
       for (int e = threadIdx.x; e < ntile; e += ncomp)
-        sm[swz(e)] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+        sm[Prog::swz(e)] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
       compute_bar(ncomp);
     } else if (g.lin_m) {
       for (int e = threadIdx.x; e < ntile; e += ncomp)
-        if (((uint32_t)e & g.lin_m) != g.lin_v) sm[swz(e)] = make_float2(0.f, 0.f);
+        if (((uint32_t)e & g.lin_m) != g.lin_v) sm[Prog::swz(e)] = make_float2(0.f, 0.f);
       compute_bar(ncomp);
     }
     // every compute thread runs the stage program, so that all of them pass

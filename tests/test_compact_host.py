@@ -62,6 +62,14 @@ def _extract():
 DRIVER = r'''
 }  // namespace sf
 using namespace sf;
+// a swizzle other than the default one (a pass may choose its own): the
+// compact store must read the tile through the one it is given
+struct Swz {
+  static uint32_t swz(uint32_t e) {
+    return e ^ ((uint32_t)(__builtin_popcount(e & 0x2b0u) & 1) << 1) ^
+           ((uint32_t)(__builtin_popcount(e & 0x150u) & 1) << 2) ^ ((uint32_t)(__builtin_popcount(e & 0x1c60u) & 1) << 3);
+  }
+};
 // stdin: m k L g  gpos[k]  n_free freepos[n_free]  nw  (word rank)[nw]  cap
 int main() {
   int m, k, L, g;
@@ -101,15 +109,15 @@ int main() {
     for (int i = 0; i < nf; i++) base |= ((t >> i) & 1u) << P.pass.freepos[i];
     geo.base = base;
     geo.tile = t;
-    // tile element e holds the value of its global index, at swz(e)
+    // tile element e holds the value of its global index, at Swz::swz(e)
     for (int e = 0; e < ntile; e++) {
       const uint32_t gi = base | runoff[e >> L] | ((uint32_t)e & cc.lmask);
-      buf[swz((uint32_t)e)] = float2{(float)gi, 1.f};
+      buf[Swz::swz((uint32_t)e)] = float2{(float)gi, 1.f};
     }
     // the store warp's order: the first round's words, then the writes
     for (int lane = 0; lane < 32; lane++) {
       const CompactWord cw = compact_word(P, geo, lane, 0);
-      compact_store_tile(P, geo, buf.data(), lane, cw);
+      compact_store_tile<Swz>(P, geo, buf.data(), lane, cw);
     }
   }
   for (long i = 0; i < (long)out.size(); i++) printf("%.1f %.1f\n", out[i].x, out[i].y);
