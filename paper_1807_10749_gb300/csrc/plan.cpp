@@ -1129,8 +1129,14 @@ std::string plan_describe(const Plan& p) {
         const PassPlan& pp = sp.passes[q];
         std::string act;
         for (int j = 0; j < pp.dev.k; j++) act += std::to_string(pp.dev.gpos[j]) + (j + 1 < pp.dev.k ? "," : "");
-        snprintf(b, sizeof b, "  pass %zu: active [%s] pins in %d out %d%s scale 2^%d\n", q, act.c_str(),
-                 pp.dev.n_pin_in, pp.dev.n_pin_out, pp.dev.gen_input ? " generated" : "",
+        auto pin_list = [](const DevPin* pins, int n) {
+          std::string r;
+          for (int i = 0; i < n; i++) r += (i ? "," : " [") + std::to_string(pins[i].pos) + (i + 1 == n ? "]" : "");
+          return r;
+        };
+        snprintf(b, sizeof b, "  pass %zu: active [%s] pins in %d%s out %d%s%s scale 2^%d\n", q, act.c_str(),
+                 pp.dev.n_pin_in, pin_list(pp.dev.pin_in, pp.dev.n_pin_in).c_str(), pp.dev.n_pin_out,
+                 pin_list(pp.dev.pin_out, pp.dev.n_pin_out).c_str(), pp.dev.gen_input ? " generated" : "",
                  (int)std::lround(std::log2(pp.dev.post_scale)));
         o += b;
         for (size_t t = 0; t < pp.stages.size(); t++) {
