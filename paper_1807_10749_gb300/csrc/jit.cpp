@@ -229,7 +229,7 @@ void gen_copy(std::ostringstream& o, const PassPlan& pp, const TileSwz& S) {
     for (int i = 0; i < n; i++)
       for (int j = 0; j < k; j++)
         if (d.gpos[j] == pins[i].pos) m |= 1u << j;
-    return m >> L;  // pins inside a run are zero-filled by the stage warps
+    return m >> L;  // pinned-out runs: zeros from the load warp; pins inside a run: the stage warps
   };
   const uint32_t rm_in = pin_mask(d.pin_in, d.n_pin_in), rm_out = pin_mask(d.pin_out, d.n_pin_out);
   uint32_t G[1 << 8], lo[1 << 8], rj[1 << 8];
@@ -261,6 +261,7 @@ void gen_copy(std::ostringstream& o, const PassPlan& pp, const TileSwz& S) {
   for (int j = 0; j < nj; j++) {
     if (rm_in) o << "if ((rl | " << (rj[j] & rm_in) << "u) == rv) ";
     o << "cp_async16(d" << lid[j] << " + " << 512u * j << "u, in + " << G[j] << "u);\n";
+    if (rm_in) o << "else st_shared_zero16(d" << lid[j] << " + " << 512u * j << "u);\n";
   }
   o << "}\n";
   // stores, eight chunks in flight per lane

@@ -213,6 +213,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// 16 zero bytes at a shared-memory address (a chunk of a pinned-out run)
+__device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0u) : "memory");
+}
 // the barrier's pending count drops by one when this thread's earlier
 // cp.async copies have landed
 __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
@@ -229,7 +233,10 @@ __device__ __forceinline__ void cp_async_arrive(uint32_t bar) {
 // zero) runs are never read and output-pinned runs never written. Every wait
 // is bounded; a timeout sets the error flag and ends the kernel.
 // Copy geometry of a tile: run r (2^L contiguous amplitudes) of a tile sits
-// at global offset runoff[r]; chunk c (elements 2c, 2c+1) at swz(2c).
+// at global offset runoff[r]; chunk c (elements 2c, 2c+1) at swz(2c). The
+// load warp writes zeros for the chunks of input-pinned runs (structural
+// zeros, never read); the compute warps zero the elements pinned out inside
+// a run.
 struct CopyCtx {
   const uint32_t* runoff;
   int L, nchunk;
@@ -258,8 +265,10 @@ struct GenericCopy {
         src[u] = in + (g.base | cc.runoff[ok[u] ? r : 0] | (uint32_t)(e & cc.lmask));
       }
 #pragma unroll
-      for (int u = 0; u < 4; u++)
+      for (int u = 0; u < 4; u++) {
         if (ok[u]) cp_async16(dst + so[u], src[u]);
+        else if (c0 + 32 * u < cc.nchunk) st_shared_zero16(dst + so[u]);  // pinned-out run
+      }
     }
   }
   static __device__ __forceinline__ void store_tile(const PassLaunch& P, const ItemGeo& g, const float2* buf,
@@ -502,9 +511,11 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
       for (int e = threadIdx.x; e < ntile; e += ncomp)
         sm[Prog::swz(e)] = (((uint32_t)e & g.lin_m) == g.lin_v) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
       compute_bar(ncomp);
-    } else if (g.lin_m) {
+    } else if (g.lin_m & (uint32_t)lmask) {
+      // pins inside a run (the load warp zero-fills the pinned-out runs)
+      const uint32_t im = g.lin_m & (uint32_t)lmask, iv = g.lin_v & (uint32_t)lmask;
       for (int e = threadIdx.x; e < ntile; e += ncomp)
-        if (((uint32_t)e & g.lin_m) != g.lin_v) sm[Prog::swz(e)] = make_float2(0.f, 0.f);
+        if (((uint32_t)e & im) != iv) sm[Prog::swz(e)] = make_float2(0.f, 0.f);
       compute_bar(ncomp);
     }
     // every compute thread runs the stage program, so that all of them pass
