@@ -601,6 +601,8 @@ def main():
                     help="shared-memory tile buffers per CTA of the specialised kernels (0: per tile size)")
     ap.add_argument("--proj-side", type=int, default=0, choices=[0, 1],
                     help="0: Eq. 1's projector on half A of every cut CZ; 1: alternating halves")
+    ap.add_argument("--cycle-segments", type=int, default=0, choices=[0, 1],
+                    help="1: segments are the cycle ranges between branch levels (no light-cone scheduling)")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1],
                     help="1: per-pass specialised kernels compiled at plan time; 0: the generic pass kernel")
     args = ap.parse_args()
@@ -636,7 +638,7 @@ def main():
                       fuse_bits=args.fuse_bits, run_bits=args.run_bits, jit=args.jit,
                       split_last=args.split_last, fp32x2=args.fp32x2, dense_finals=args.dense_finals,
                       projector_side=args.proj_side, tile_buffers=args.tile_buffers,
-                      batch_paths=args.batch_paths)
+                      batch_paths=args.batch_paths, cycle_segments=args.cycle_segments)
     t_plan = time.perf_counter() - t_plan
     fsel = sfsim.selection("fraction", fidelity=FIDELITY, seed=SEED)
     n_sel, f_actual = sfsim.sf_selection_size(plan.handle, fsel)

@@ -136,7 +136,13 @@ typedef struct {
                                its own) or 2 (half the memory, so a third CTA of
                                2^12-amplitude tiles fits on an SM); 0 = 2 for tiles
                                of up to 2^12 amplitudes, 3 above */
-  int32_t reserved[3];
+  int32_t cycle_segments;   /* 0 (default) = each gate runs in the segment of the
+                               deepest branch level whose light cone holds it
+                               (the gates a level's branch operators commute
+                               with run once in the parent node, for all its
+                               children); 1 = segments are the cycle ranges
+                               between consecutive branch levels */
+  int32_t reserved[2];
 } sf_plan_opts;
 
 /* Which half of a cut CZ carries the projector of Eq. 1. CZ is symmetric, so

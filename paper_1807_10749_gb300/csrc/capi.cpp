@@ -195,6 +195,7 @@ int sf_plan_create(const sf_circuit* c, const sf_plan_opts* opts, sf_plan** out)
     sf::fail(SF_EINVAL, "unknown projector side");
   if (o.tile_buffers != 0 && o.tile_buffers != 2 && o.tile_buffers != 3)
     sf::fail(SF_EINVAL, "tile_buffers must be 0, 2 or 3");
+  if (o.cycle_segments != 0 && o.cycle_segments != 1) sf::fail(SF_EINVAL, "cycle_segments must be 0 or 1");
   sf::Plan* p = sf::plan_create(c->c, o);
   sf_plan* h = new sf_plan();
   h->p = p;

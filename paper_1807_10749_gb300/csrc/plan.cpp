@@ -756,6 +756,60 @@ void plan_segment(int m, const std::vector<HOp>& seg_ops, std::vector<Pin> pins,
 
 }  // namespace
 
+// A gate whose matrix is diagonal commutes with the diagonal branch
+// operators (Eq. 1's projectors and Z factors).
+bool gate_diag(const Gate& g) {
+  const int d = g.nq() == 2 ? 4 : 2;
+  for (int r = 0; r < d; r++)
+    for (int q = 0; q < d; q++)
+      if (r != q && !near(g.m[r * d + q], 0, 0)) return false;
+  return true;
+}
+
+// Light cones of the branch levels. At level l each cut gate is replaced,
+// on each half, by one of its term factors on the cut qubit: a projector or
+// Z for Eq. 1, general 2x2 factors for the Schmidt and four-block forms. A
+// later gate of that half commutes with the factors unless it is causally
+// after them: the cone of level l starts at each cut qubit, with its first
+// non-diagonal gate after the level (at the level itself when the factors
+// are not diagonal), and takes in every qubit that a later gate couples to a
+// qubit already in it. A gate in no cone of a deeper level than l can run
+// before that level's branching, in the node every child of it shares. The
+// result: per gate, the deepest level (1-based) whose cone holds it, 0 for
+// none; cross gates are not scheduled this way.
+template <class InB>
+std::vector<int> cone_depths(const Circuit& c, const Plan& P, const InB& inB) {
+  std::vector<int> depth(c.gates.size(), 0);
+  std::vector<char> is_cross(c.gates.size(), 0);
+  for (const auto& x : P.cross) is_cross[x.gate_index] = 1;
+  for (size_t l = 0; l < P.levels.size(); l++) {
+    const Level& L = P.levels[l];
+    for (int side = 0; side < 2; side++) {
+      std::vector<char> in(c.n, 0), cut(c.n, 0);
+      for (int i = 0; i < L.n_cross; i++) {
+        const CrossGate& x = P.cross[L.first_cross + i];
+        const int q = side ? x.qb : x.qa;
+        cut[q] = 1;
+        for (int t = 0; t < x.nterm; t++) {
+          const cd* f = side ? x.fb[t] : x.fa[t];
+          if (!near(f[1], 0, 0) || !near(f[2], 0, 0)) in[q] = 1;
+        }
+      }
+      for (size_t i = 0; i < c.gates.size(); i++) {
+        const Gate& g = c.gates[i];
+        if (g.cycle < L.cycle || is_cross[i] || (int)inB(g.q0) != side) continue;
+        bool hit = in[g.q0] || (g.nq() == 2 && in[g.q1]);
+        if (!hit && (cut[g.q0] || (g.nq() == 2 && cut[g.q1])) && !gate_diag(g)) hit = true;
+        if (!hit) continue;
+        in[g.q0] = 1;
+        if (g.nq() == 2) in[g.q1] = 1;
+        depth[i] = std::max(depth[i], (int)l + 1);
+      }
+    }
+  }
+  return depth;
+}
+
 // ------------------------------------------------------------ plan create
 // Plan a segment. With an automatic tile size (tile_bits option 0) the
 // candidates are 2^12 and 2^13 amplitudes, with an automatic run width
@@ -882,13 +936,16 @@ Plan* plan_create(const Circuit& c, const sf_plan_opts& o) {
       for (size_t p = 0; p < order.size(); p++) H.pos_of[order[p]] = (int)p;
       H.seg_ops.assign(nL + 1, {});
     }
-    // segment of a gate: the number of levels whose cycle <= gate cycle
-    // (local gates of a level's cycle run after its cross gates)
+    // segment of a gate. By cycles: the number of levels whose cycle <= gate
+    // cycle (local gates of a level's cycle run after its cross gates). By
+    // light cones (default): the deepest level whose cone holds the gate.
+    const std::vector<int> cone = o.cycle_segments ? std::vector<int>() : cone_depths(c, *P, inB);
     std::vector<cd> seg_global(2 * (nL + 1), cd(1.0));
     for (size_t i = 0; i < c.gates.size(); i++) {
       const Gate& g = c.gates[i];
       int s = 0;
       while (s < nL && P->levels[s].cycle <= g.cycle) s++;
+      if (!cone.empty() && !xindex.count((int)i)) s = cone[i];
       auto it = xindex.find((int)i);
       if (it != xindex.end()) {
         const CrossGate& x = P->cross[it->second];

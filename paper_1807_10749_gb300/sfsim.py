@@ -59,7 +59,7 @@ class sf_plan_opts(ctypes.Structure):
                 ("jit", ctypes.c_int32), ("split_last", ctypes.c_int32), ("fp32x2", ctypes.c_int32),
                 ("dense_finals", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("projector_side", ctypes.c_int32), ("tile_buffers", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("cycle_segments", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class sf_path_sel(ctypes.Structure):

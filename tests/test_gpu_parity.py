@@ -284,12 +284,13 @@ def test_5x6_full_sum_porter_thomas(jit):
 
 
 # ---------------------------------------------------------------- 6x7 (C3)
-@pytest.mark.parametrize("kind,split", [("cz", 0), ("cz", 1), ("haar", 0)])
-def test_6x7_path_list_matches_oracle(kind, split, jit):
+@pytest.mark.parametrize("kind,split,cyc", [("cz", 0, 0), ("cz", 1, 0), ("haar", 0, 0), ("cz", 0, 1)])
+def test_6x7_path_list_matches_oracle(kind, split, cyc, jit):
     """64 paths x 4096 bitstrings. CZ: 48 random paths and one whole group of
     the folded last level (16 leaves, contracted in closed form). Haar (every
     cut gate branches 4 ways): 32 random paths and 32 leaves of one group of
-    256 (the partial-group form of the contraction)."""
+    256 (the partial-group form of the contraction). cyc = 1: segments by
+    cycle ranges instead of light cones."""
     w, text = workload("6x7_d26", haar=(kind == "haar"))
     c = ocirc.parse(text)
     setup = sim.SFSetup(c, w["side_b_mask"])
@@ -302,9 +303,10 @@ def test_6x7_path_list_matches_oracle(kind, split, jit):
     ref = per.sum(axis=0)
     # split = 0: the level before the folded last level runs inside the last
     # program; split = 1: as its own segment with the node in between
-    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], split_last=split)
+    p = sfsim.Plan(text, jit=jit, side_b_mask=w["side_b_mask"], split_last=split, cycle_segments=cyc)
     amp, _ = p.amplitudes(bits, sfsim.selection("list", ids=ids))
-    check_close(amp, ref, 42, f"6x7 {kind} split={split} {len(ids)} paths", path_scale=path_scale(per))
+    check_close(amp, ref, 42, f"6x7 {kind} split={split} cycle_segments={cyc} {len(ids)} paths",
+                path_scale=path_scale(per))
     p.close()
 
 

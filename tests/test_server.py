@@ -140,7 +140,9 @@ def test_queued_requests_on_one_plan_run_as_one_batch(plans):
     srv = sfsim.sf_server_create(0, 1)
     try:
         b_long = inputs.random_bitstrings(n_long, 500, 9)
-        t0 = sfsim.sf_server_submit(srv, long_plan.handle, b_long, sfsim.selection("fraction", fidelity=1 / 32))
+        # 2^23 paths: seconds of work, so the worker is still busy with it
+        # when the five requests below have been submitted
+        t0 = sfsim.sf_server_submit(srv, long_plan.handle, b_long, sfsim.selection("fraction", fidelity=1 / 4))
         time.sleep(0.2)   # the long request occupies the worker
         tickets = [sfsim.sf_server_submit(srv, plan.handle, b, s) for b, s in reqs]
         sfsim.sf_server_wait(srv, t0, len(b_long))
