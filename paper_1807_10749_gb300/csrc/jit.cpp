@@ -205,6 +205,49 @@ std::string deposit(const int8_t* pos, int nbits) {
   return e.empty() ? "0u" : e;
 }
 
+// The geometry of a work item (item_geo in pass_common.cuh) with the pass's
+// free positions, active set and pin positions as constants: the tile number
+// deposited into the free positions, the pin values read from the path's
+// digits, and the pins' masks on tile-local bits.
+void gen_geo(std::ostringstream& o, const PassPlan& pp) {
+  const DevPass& d = pp.dev;
+  uint32_t active = 0;
+  for (int j = 0; j < d.k; j++) active |= 1u << d.gpos[j];
+  o << "static __device__ __forceinline__ ItemGeo geo(const PassLaunch& P, int64_t item, int) {\n"
+    << "ItemGeo g;\n"
+    << "const uint32_t nn = (uint32_t)P.n_nodes, it32 = (uint32_t)item;\n"
+    << "const uint32_t tid = it32 / nn;\n"
+    << "g.node = (int)(it32 - tid * nn);\ng.tile = tid;\ng.path = P.nodes[g.node].path;\n"
+    << "uint32_t pv = 0, lv = 0, ov = 0;\n(void)pv; (void)lv; (void)ov;\n";
+  uint32_t lm = 0, om = 0;
+  auto pin = [&](const DevPin& q, bool out) {
+    std::string val;
+    if (q.xi < 0) {
+      val = std::to_string((unsigned)q.v[0]) + "u";
+    } else {
+      char b[160];
+      std::snprintf(b, sizeof b, "((0x%xu >> (8 * digit_of(P.xshift, P.xbits, g.path, %d))) & 1u)",
+                    (uint32_t)q.v[0] | (uint32_t)q.v[1] << 8 | (uint32_t)q.v[2] << 16 | (uint32_t)q.v[3] << 24, q.xi);
+      val = b;
+    }
+    int j = -1;
+    for (int t = 0; t < d.k; t++)
+      if (d.gpos[t] == q.pos) j = t;
+    o << "{ const uint32_t v = " << val << ";";
+    if (!out) o << " pv |= v << " << (int)q.pos << ";";
+    if (j >= 0) {
+      o << (out ? " ov" : " lv") << " |= v << " << j << ";";
+      (out ? om : lm) |= 1u << j;
+    }
+    o << " }\n";
+  };
+  for (int i = 0; i < d.n_pin_in; i++) pin(d.pin_in[i], false);
+  for (int i = 0; i < d.n_pin_out; i++) pin(d.pin_out[i], true);
+  o << "g.base = (" << deposit(d.freepos, d.n_free) << ") | (pv & " << (~active) << "u);\n"
+    << "g.lin_m = " << lm << "u; g.lin_v = lv; g.lout_m = " << om << "u; g.lout_v = ov;\n"
+    << "return g;\n}\n";
+}
+
 // The tile copies of one pass with its geometry as constants. Lane l moves
 // chunks c = l + 32 j (elements 2c, 2c+1). The global offset of a chunk is
 // the deposit of its tile bits into the pass's index positions, a lane part
@@ -740,6 +783,7 @@ std::string gen_pass(const PassPlan& pp, const std::string& name, bool pack, int
     o << "}\ncompute_bar(ncomp);\n";
   }
   o << "}\n";
+  gen_geo(o, pp);
   gen_copy(o, pp, S);
   o << "};\n}  // namespace sf\n";
   const int threads = (((1 << (k - R)) + 31) / 32) * 32 + 64;  // stage warps + the two copy warps

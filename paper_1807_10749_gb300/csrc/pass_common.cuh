@@ -248,6 +248,9 @@ struct CopyCtx {
 // swz() and its own copies.
 struct GenericCopy {
   static __device__ __forceinline__ uint32_t swz(uint32_t e) { return sf::swz(e); }
+  static __device__ __forceinline__ ItemGeo geo(const PassLaunch& P, int64_t item, int tiles_log2) {
+    return item_geo(P, item, tiles_log2);
+  }
   static __device__ __forceinline__ void load_tile(const PassLaunch& P, const ItemGeo& g, uint32_t dst, int lane,
                                                    const CopyCtx& cc) {
     const float2* in = reinterpret_cast<const float2*>(P.nodes[g.node].in);
@@ -416,7 +419,7 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
     // --------------------------------------------------------------- loads
     // The load warp takes the CTA's items: its first is blockIdx.x, every
     // later one comes from the launch's counter (taken one item ahead, so
-    // the atomic's latency hides behind the wait for a free buffer). CTAs
+    // the atomic's latency hides behind the tile's copies). CTAs
     // that get through their items faster take more of them, so the CTAs
     // sharing an SM finish together. The warp computes each item's geometry
     // once and publishes it in geo[b]; after the last item it publishes an
@@ -427,6 +430,14 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
     uint32_t ahead = 0;  // lane 0: the counter's value for the next item
     for (int i = 0;; i++) {
       const int b = i % NBUF;
+      // the item and its geometry do not depend on the buffer: found before
+      // waiting for it to be free
+      if (i > 0) it = (int64_t)gridDim.x + (int64_t)__shfl_sync(0xffffffffu, ahead, 0);
+      const bool last = it >= items;
+      if (lane == 0 && !last) ahead = atomicAdd(P.work, 1u);
+      ItemGeo g{};
+      if (!last) g = Prog::geo(P, it, tiles_log2);
+      else g.node = -1;
       if (i >= NBUF && !mbar_wait(smem_u32(&freeb[b]), (uint32_t)((i / NBUF - 1) & 1))) {
         if (lane == 0) {
           abort_flag = 1;
@@ -435,12 +446,6 @@ __device__ __forceinline__ void pass_body(const PassLaunch& P) {
         break;
       }
       if (*(volatile int*)&abort_flag) break;
-      if (i > 0) it = (int64_t)gridDim.x + (int64_t)__shfl_sync(0xffffffffu, ahead, 0);
-      const bool last = it >= items;
-      if (lane == 0 && !last) ahead = atomicAdd(P.work, 1u);
-      ItemGeo g{};
-      if (!last) g = item_geo(P, it, tiles_log2);
-      else g.node = -1;
       if (lane == 0) geo[b] = g;
       if (!last && !d.gen_input) Prog::load_tile(P, g, smem_u32(bufs + b * ntile), lane, cc);
       cp_async_arrive(smem_u32(&full[b]));
