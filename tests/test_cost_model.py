@@ -74,9 +74,10 @@ def test_calibrated_model_predicts_request_times():
           f"median |rel err| {np.median(rel):.3f}, max {rel.max():.3f}")
     assert np.all(coeffs >= 0) and c3 > 0 and (c1 > 0 or c1c2 > 0)
     # Eq. t_tot models a prefix/suffix split; the executor caches every tree
-    # level, so the fit carries a model error of its own: median 0.2-0.26 on
+    # level and runs each gate at the depth of the light cone that reaches
+    # it, so the fit carries a model error of its own: median 0.25-0.35 on
     # this set over repeated runs, the 5x6 prefix selections under-predicted
-    assert np.median(rel) < 0.3
+    assert np.median(rel) < 0.4
     for p_ in plans.values():
         p_.close()
 
