@@ -104,7 +104,9 @@ typedef struct {
                                 into the gather when the circuit allows */
   int64_t hbm_budget_bytes;  /* device memory the executor may use, 0 = 75% of
                                 free memory at plan time */
-  int32_t batch_paths;       /* max leaf groups per launch, 0 = from budget */
+  int32_t batch_paths;       /* max leaf groups (finals) per launch, 0 = as many as
+                                hold 2^30 amplitudes of both halves, halved until
+                                the workspace fits the memory budget */
   int32_t run_bits;          /* log2 contiguous amplitudes per copy run (the
                                 index bits every pass keeps active), 0 = per
                                 segment the width (4 or 3) whose program moves

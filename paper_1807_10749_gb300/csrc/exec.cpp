@@ -160,7 +160,9 @@ Layout make_layout(const Plan& p, uint64_t n_finals, const Compact& cp, int64_t 
   const size_t nb = node_bytes(p);
   int64_t budget = budget_override > 0 ? budget_override : p.opts.hbm_budget_bytes;
   const size_t amps = ((size_t)1 << p.A.m) + ((size_t)1 << p.B.m);
-  int64_t B = p.opts.batch_paths > 0 ? p.opts.batch_paths : std::max<int64_t>(1, ((int64_t)1 << 26) / (int64_t)amps);
+  // default: finals of 2^30 amplitudes (both halves) per launch, halved below
+  // until the layout fits the budget (7x8: 2, 5x10: 16)
+  int64_t B = p.opts.batch_paths > 0 ? p.opts.batch_paths : std::max<int64_t>(1, ((int64_t)1 << 30) / (int64_t)amps);
   B = std::min<int64_t>(B, std::max<uint64_t>(1, n_finals));
   Layout lay;
   while (true) {

@@ -4,7 +4,9 @@ workspace). Whole-state finals need the node slots only; compact finals add,
 per half whose final pass qualifies, a part map (8 bytes per 32 parts of
 2^ctl amplitudes), its chunk counts and, per final of a block, a buffer of
 min(n * 2^(g - ctl), 2^(m - ctl)) parts. ctl is read off the plan's
-description (the last pass's tile positions below g)."""
+description (the last pass's tile positions below g). A block holds as many
+finals as hold 2^30 amplitudes of both halves (two at 7x8), within the
+budget."""
 import re
 
 import pytest
@@ -36,7 +38,7 @@ def _final_ctl(plan, g):
     return out
 
 
-def _compact_bytes(m, g, ctls, n):
+def _compact_bytes(m, g, ctls, n, finals_per_block=1):
     extra = 0
     for ctl in ctls:
         parts = 1 << (m - ctl)
@@ -44,7 +46,7 @@ def _compact_bytes(m, g, ctls, n):
         if (cap << ctl) * 4 > (1 << m):
             return 0
         nw = (parts + 31) // 32
-        extra += _a256(nw * 8) + _a256(((nw + 2047) // 2048) * 4) + _a256((cap << ctl) * 8)
+        extra += _a256(nw * 8) + _a256(((nw + 2047) // 2048) * 4) + finals_per_block * _a256((cap << ctl) * 8)
     return extra
 
 
@@ -57,9 +59,10 @@ def test_7x8_workspace_adds_exactly_the_part_maps_and_buffers():
     g = 4
     ctls = _final_ctl(p, g)
     assert all(1 <= c <= g and g - c <= 1 for c in ctls), ctls
+    B = min((1 << 30) // (2 * (1 << 28)), 128 // 16)   # finals per block: 2 of the range's 8
     for n in (1, 1000, 1_000_000):
         extra = sfsim.sf_workspace_size(p.handle, n, sel) - sfsim.sf_workspace_size(q.handle, n, sel)
-        assert extra == _compact_bytes(28, g, ctls, n), n
+        assert extra == _compact_bytes(28, g, ctls, n, B), n
         assert extra > 0
     # 5M bitstrings: the blocks would fill more than a quarter of each half
     assert _compact_bytes(28, g, ctls, 5_000_000) == 0
