@@ -505,6 +505,7 @@ static int host_form(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_
     hb.stream = st;
   }
   cudaStream_t hst = (cudaStream_t)hb.stream;
+  sf::ExecCtx ctx;  // the plan's defaults; a smaller layout when memory is short
   if (hb.ws_bytes < need) {
     if (hb.ws) {
       sf::exec_forget_workspace(hb.ws);
@@ -512,8 +513,12 @@ static int host_form(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_
     }
     hb.ws = nullptr;
     hb.ws_bytes = 0;
-    cuda_check(cudaMalloc(&hb.ws, need), "cudaMalloc workspace");
-    hb.ws_bytes = need;
+    std::vector<sf::ExecReq> one(1);
+    one[0].rs = rs;
+    one[0].n = n;
+    size_t got = 0;
+    ctx.budget = sf::exec_alloc_workspace(*h->p, one, 0, &hb.ws, &got);
+    hb.ws_bytes = got;
   }
   if (hb.cap_n < n) {
     if (hb.bits) cudaFree(hb.bits);
@@ -526,7 +531,7 @@ static int host_form(sf_plan* h, const uint64_t* bits, int64_t n, const sf_path_
     hb.cap_n = n;
   }
   cuda_check(cudaMemcpyAsync(hb.bits, bits, (size_t)n * 8, cudaMemcpyHostToDevice, hst), "cudaMemcpyAsync");
-  sf::exec_run(*h->p, hb.bits, n, *sel, hb.out, 0, hb.ws, hb.ws_bytes, hst, true);
+  sf::exec_run(*h->p, hb.bits, n, *sel, hb.out, 0, hb.ws, hb.ws_bytes, hst, true, &ctx);
   if (prob) {
     sf::launch_prob(hb.out, n, divide_by_f ? (fa > 0 ? 1.0 / fa : 0.0) : 1.0, hb.probs(n), hst);
     cuda_check(cudaMemcpyAsync(out, hb.probs(n), (size_t)n * 8, cudaMemcpyDeviceToHost, hst), "cudaMemcpyAsync");

@@ -430,6 +430,37 @@ size_t exec_workspace_bytes(const Plan& p, const std::vector<ExecReq>& reqs, int
   return lay.bytes + 256;
 }
 
+// Allocate a workspace for these requests. The plan's layout takes as many
+// finals per launch as its memory budget allows; when the device has less
+// free memory than that budget assumed (other allocations since the plan was
+// made), the layout's budget is halved - fewer finals per launch - until the
+// allocation succeeds, or fails with SF_ENOMEM once one final per block does
+// not fit. Returns the budget the layout used (0: the plan's own), which the
+// caller passes to exec_run (ExecCtx::budget).
+int64_t exec_alloc_workspace(const Plan& p, const std::vector<ExecReq>& reqs, int64_t budget, void** ws,
+                             size_t* bytes) {
+  size_t need = exec_workspace_bytes(p, reqs, budget);
+  while (true) {
+    const cudaError_t e = cudaMalloc(ws, need);
+    if (e == cudaSuccess) {
+      *bytes = need;
+      return budget;
+    }
+    if (e != cudaErrorMemoryAllocation) fail(SF_ECUDA, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    const int64_t next = (int64_t)((need - 256) / 2);
+    size_t need2 = 0;
+    try {
+      need2 = exec_workspace_bytes(p, reqs, next);
+    } catch (const Error&) {
+      fail(SF_ENOMEM, "cudaMalloc workspace: out of memory (" + std::to_string(need) + " bytes)");
+    }
+    if (need2 >= need) fail(SF_ENOMEM, "cudaMalloc workspace: out of memory (" + std::to_string(need) + " bytes)");
+    budget = next;
+    need = need2;
+  }
+}
+
 size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget) {
   std::vector<ExecReq> one(1);
   double fa;

@@ -213,8 +213,13 @@ void run_batch(sf_server& s, std::vector<std::shared_ptr<Request>>& b, size_t ws
   int code = 0;
   std::string msg;
   std::vector<sf::ExecReq> v(b.size());
+  int64_t layout_budget = 0;  // the plan's own, unless the device is short of memory
   try {
     cuda_ok(cudaSetDevice(s.device), "cudaSetDevice");
+    for (size_t i = 0; i < b.size(); i++) {
+      v[i].rs = b[i]->rs;
+      v[i].n = (int64_t)b[i]->bits.size();
+    }
     if (pool.ws_bytes < ws_need) {
       if (pool.ws) {
         sf::exec_forget_workspace(pool.ws);
@@ -222,10 +227,11 @@ void run_batch(sf_server& s, std::vector<std::shared_ptr<Request>>& b, size_t ws
       }
       pool.ws = nullptr;
       pool.ws_bytes = 0;
-      cuda_ok(cudaMalloc(&pool.ws, ws_need), "cudaMalloc workspace");
-      pool.ws_bytes = ws_need;
       sf::exec_free_cache(*cache);  // its buffers were in the old workspace
       *cache = nullptr;
+      size_t got = 0;
+      layout_budget = sf::exec_alloc_workspace(*b[0]->plan, v, 0, &pool.ws, &got);
+      pool.ws_bytes = got;
     }
     if (pool.cap_n < ntot) {
       if (pool.bits) cudaFree(pool.bits);
@@ -260,6 +266,7 @@ void run_batch(sf_server& s, std::vector<std::shared_ptr<Request>>& b, size_t ws
     ctx.cache_slot = cache;
     ctx.profile = false;
     ctx.err = d_err;
+    ctx.budget = layout_budget;
     sf::exec_run(*b[0]->plan, v, pool.ws, pool.ws_bytes, st, true, &ctx);
     at = 0;
     for (size_t i = 0; i < b.size(); i++) {

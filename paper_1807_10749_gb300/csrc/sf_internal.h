@@ -260,6 +260,10 @@ struct ExecReq {
 };
 size_t exec_workspace_bytes(const Plan& p, int64_t n, const sf_path_sel& s, int64_t budget = 0);
 size_t exec_workspace_bytes(const Plan& p, const std::vector<ExecReq>& reqs, int64_t budget = 0);
+// cudaMalloc of a workspace for reqs, with fewer finals per launch when the
+// device's free memory is short; returns the layout budget used.
+int64_t exec_alloc_workspace(const Plan& p, const std::vector<ExecReq>& reqs, int64_t budget, void** ws,
+                             size_t* bytes);
 void exec_run(Plan& p, const uint64_t* d_bits, int64_t n, const sf_path_sel& s, double* d_out,
               int accumulate, void* ws, size_t ws_bytes, void* stream, bool keep_cache,
               ExecCtx* ctx = nullptr);
