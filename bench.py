@@ -761,7 +761,7 @@ def main():
         suite = other_configs(sfsim, inputs, peak, stream)
         if not args.no_serve:
             torch.cuda.empty_cache()   # the server allocates its own buffers
-        serving = serving_window(sfsim, inputs, coeffs)
+            serving = serving_window(sfsim, inputs, coeffs)
 
     if rank == 0:
         achieved = (pass_b / pass_s) / 1e9 if pass_s > 0 else None
