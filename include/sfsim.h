@@ -268,8 +268,12 @@ SF_API int sf_selection_ids(const sf_plan* p, const sf_path_sel* sel, uint64_t* 
 
 /* Amplitudes, host buffers: out_amps[2*i], out_amps[2*i+1] = sum over the
  * selected paths of A_j[x_A] * B_j[x_B] for bitstrings[i] (Eq. 2 / Eq. 3, no
- * renormalisation by f). out_f_actual may be NULL. Allocates and frees its
- * device memory inside the call; blocks until done. */
+ * renormalisation by f). out_f_actual may be NULL. Allocates its device
+ * memory inside the call (kept with the plan for the next call, freed by
+ * sf_plan_drop_resident or sf_plan_destroy); blocks until done. When the
+ * device has less free memory than the plan's budget assumed, the workspace
+ * takes fewer finals per launch (same results); SF_ENOMEM when one does not
+ * fit. */
 SF_API int sf_amplitudes(sf_plan* p, const uint64_t* bitstrings, int64_t n, const sf_path_sel* sel,
                   double* out_amps, double* out_f_actual);
 
@@ -405,7 +409,8 @@ SF_API int sf_amplitudes_device_noalloc(sf_plan* p, const uint64_t* d_bitstrings
 /* Request server (continuous batching): requests are admitted while their
  * device footprint fits hbm_budget_bytes; admitted requests run concurrently
  * on their own streams. Each request's result equals sf_amplitudes on the same
- * input. */
+ * input. A worker whose workspace allocation fails for lack of free memory
+ * lays it out with fewer finals per launch. */
 SF_API int sf_server_create(int64_t hbm_budget_bytes, int max_concurrent, sf_server** out);
 /* Copies bitstrings and the selection's list. The plan must outlive the
  * request. */
